@@ -1,0 +1,181 @@
+/*
+ * libtt — quantics tensor-train arithmetic on sm_103a (C ABI).
+ *
+ * Every entry point is an operation of the trainsum paper (arXiv 2602.20226):
+ *   tt_apply_mpo   'ij,j->i' of an MPO and a TT, core by core     Section 3.1, Eq. (quant_sum), Eq. (einsum)
+ *   tt_hadamard    'i,i->i' of two TTs (element-wise product)      Section 3.1, Eq. (einsum)
+ *   tt_round       normalisation centre to the left end, then a
+ *                  truncated decomposition at each bond            Section 3.2 (decomposition algorithms);
+ *                                                                  TensorTrain.truncate in Section 6
+ *   tt_inner       'i,i->' (all indices contracted)                Section 3.1, Eq. (einsum)
+ *   tt_eval        entries at index tuples (exact sampling)        Section 3.4; evaluate in Section 6
+ * and the hand-written adjoint of each (the *_backward calls).
+ *
+ * Data layout (all row-major, all device memory unless stated):
+ *   TT core k      G_k[r_{k-1}][d_k][r_k], r_0 = r_L = 1, site 1 = most significant digit
+ *                  (Section 2, Eq. (quantization)).
+ *   MPO core k     W_k[a_{k-1}][d_k (out i)][d_k (in j)][a_k].
+ *   Bond flatten   a product bond is xi = mu * R_second + nu (first operand major),
+ *                  the flatten xi = (mu, nu) after Eq. (einsum).
+ *
+ * Ownership: the caller allocates every buffer (device cores, device workspace,
+ * host descriptor arrays) and keeps it alive until the stream work has finished.
+ * The library never allocates or frees device memory.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls enqueue work on that stream.  Calls that return a scalar or a
+ * data-dependent rank to the host (tt_round, tt_inner) synchronise the stream.
+ *
+ * Errors: every call returns a tt_status.  Arguments are validated on the host
+ * before anything is enqueued; on a validation error nothing is launched.
+ * tt_last_error() returns a message for the last failing call of this thread.
+ */
+#ifndef LIBTT_TT_H
+#define LIBTT_TT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_ARG = 1,          /* NULL pointer or invalid scalar argument */
+  TT_ERR_SHAPE = 2,        /* inconsistent lengths, modes or ranks */
+  TT_ERR_DTYPE = 3,        /* unsupported or mismatched element type */
+  TT_ERR_UNSUPPORTED = 4,  /* size beyond a documented limit */
+  TT_ERR_WORKSPACE = 5,    /* workspace smaller than the *_workspace_size query */
+  TT_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+  TT_ERR_NUMERIC = 7,      /* NaN/Inf met, or the Jacobi SVD hit its sweep cap */
+  TT_ERR_TIMEOUT = 8       /* a bounded device-side wait expired */
+} tt_status;
+
+typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
+
+/* Arithmetic form of tt_round.
+ *   TT_PREC_FP64    everything in FP64 (the plain FP64 GPU form; TT_F64 cores).
+ *   TT_PREC_MIXED   TT_F32 cores; QR panels in FP32, the dense core GEMMs on the
+ *                   tensor cores in TF32 with a 3-term hi/lo split and FP32
+ *                   accumulation; bond SVDs, the truncation decision and the norm
+ *                   in FP64. */
+typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_prec;
+
+/* Limits of this build. */
+#define TT_MAX_SITES 128 /* L <= TT_MAX_SITES */
+#define TT_MAX_MODE 16   /* d_k <= TT_MAX_MODE */
+
+/* A tensor train.  Host-side descriptor of device cores.
+ *   L      number of sites (1 <= L <= TT_MAX_SITES)
+ *   dtype  tt_dtype of every core
+ *   d      host [L], mode sizes d_k >= 1
+ *   ranks  host [L+1], ranks[0] = ranks[L] = 1; output calls write it
+ *   cores  host [L] array of device pointers; core k holds ranks[k]*d[k]*ranks[k+1]
+ *          elements (for outputs of tt_round: room for the input's ranks). */
+typedef struct {
+  int32_t L;
+  int32_t dtype;
+  const int32_t* d;
+  int64_t* ranks;
+  void* const* cores;
+} tt_train;
+
+/* A matrix product operator with square cores W_k[a][d_k][d_k][a'].
+ * Fields as in tt_train; ranks are the operator bonds a_k. */
+typedef struct {
+  int32_t L;
+  int32_t dtype;
+  const int32_t* d;
+  const int64_t* ranks;
+  void* const* cores;
+} tt_mpo;
+
+/* Message for the last failing call of the calling thread ("" if none). */
+const char* tt_last_error(void);
+
+/* Library version string. */
+const char* tt_version(void);
+
+/* y = W x ('ij,j->i', Section 3.1, Eq. (quant_sum) and Eq. (einsum)).
+ *   Y_k[(a, r), i, (a', r')] = sum_j W_k[a, i, j, a'] G_k[r, j, r'],  xi = a * R_x + r.
+ * y->ranks is written (ranks a_k * r_k); y->cores must hold those sizes.
+ * W, x, y share dtype.  One launch for all sites.  Asynchronous. */
+int tt_apply_mpo(const tt_mpo* W, const tt_train* x, tt_train* y, void* stream);
+
+/* z = x (.) y ('i,i->i', Section 3.1, Eq. (einsum)).
+ *   Z_k[(r, s), i, (r', s')] = X_k[r, i, r'] Y_k[s, i, s'].
+ * z->ranks is written (ranks r_k * s_k).  Asynchronous. */
+int tt_hadamard(const tt_train* x, const tt_train* y, tt_train* z, void* stream);
+
+/* Device workspace (bytes) that tt_round needs for input x in form prec. */
+size_t tt_round_workspace_size(const tt_train* x, int32_t prec);
+
+/* out = round(x, eps, max_rank): TT rounding (Section 3.2).
+ *   1. right-to-left sweep, k = L..2: LQ of C_k as r_{k-1} x (d_k r_k) by Householder
+ *      QR of its transpose; C_k <- Q, C_{k-1} <- C_{k-1} L.  ||x|| = ||C_1||_F.
+ *   2. left-to-right sweep, k = 1..L-1: QR of C_k as (r_{k-1} d_k) x r_k, SVD of R
+ *      (one-sided Jacobi, FP64), r' = smallest r' >= 1 whose discarded singular
+ *      values have 2-norm <= eps ||x|| / sqrt(L-1), capped at max_rank (<= 0: no cap);
+ *      C_k <- Q U[:, :r'], C_{k+1} <- (S V^T)[:r'] C_{k+1}.
+ * Guarantees ||x - out|| <= eps ||x|| when the cap does not bind.
+ *   x      input TT (not modified); TT_F64 for TT_PREC_FP64, TT_F32 for TT_PREC_MIXED
+ *   out    out->cores[k] must hold x's ranks[k]*d[k]*ranks[k+1] elements; the result
+ *          is written compactly with its own ranks, which go to out->ranks (host).
+ *   norm_out  host pointer or NULL; receives ||x|| (FP64)
+ *   workspace/ws_bytes  device scratch of at least tt_round_workspace_size bytes.
+ * Synchronises the stream (the truncated ranks are read back after every bond).
+ * Returns TT_ERR_NUMERIC if a Jacobi SVD did not converge within its sweep cap
+ * (the output is still written and still meets the error bound). */
+int tt_round(const tt_train* x, double eps, int64_t max_rank, int32_t prec, tt_train* out,
+             double* norm_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Device workspace (bytes) that tt_inner / tt_inner_backward need. */
+size_t tt_inner_workspace_size(const tt_train* x, const tt_train* y);
+
+/* <x, y> = E_L with E_0 = 1, E_k = sum_i X_k(i)^T E_{k-1} Y_k(i)  ('i,i->').
+ * Environments are accumulated in FP64 for both dtypes.  *out (host) receives the
+ * value; the call synchronises the stream. */
+int tt_inner(const tt_train* x, const tt_train* y, double* out, void* workspace, size_t ws_bytes,
+             void* stream);
+
+/* values[s] = G_1[:, i_1^s, :] ... G_L[:, i_L^s, :]  (exact evaluation).
+ *   digits  device uint8 [n][L], digit k of sample s at digits[s*L + k] (< d_k)
+ *   values  device [n], x's dtype.  Asynchronous. */
+int tt_eval(const tt_train* x, const uint8_t* digits, int64_t n, void* values, void* stream);
+
+/* ---- adjoints: gradients are ACCUMULATED (+=) into caller-initialised cores ---- */
+
+/* dG_k[r, j, r'] += sum_{a, a', i} W_k[a, i, j, a'] dY_k[(a, r), i, (a', r')]
+ * dW_k[a, i, j, a'] += sum_{r, r'} G_k[r, j, r'] dY_k[(a, r), i, (a', r')]   (dW may be NULL).
+ * dy has y's shape (ranks a_k r_k).  Asynchronous. */
+int tt_apply_mpo_backward(const tt_mpo* W, const tt_train* x, const tt_train* dy, tt_mpo* dW,
+                          tt_train* dx, void* stream);
+
+/* dX_k[r, i, r'] += sum_{s, s'} dZ_k[(r, s), i, (r', s')] Y_k[s, i, s'], and dY likewise
+ * (either gradient may be NULL).  Asynchronous. */
+int tt_hadamard_backward(const tt_train* x, const tt_train* y, const tt_train* dz, tt_train* dx,
+                         tt_train* dy, void* stream);
+
+/* dX_k(i) += dout E^L_{k-1} Y_k(i) (E^R_k)^T,  dY_k(i) += dout (E^L_{k-1})^T X_k(i) E^R_k,
+ * with left environments E^L and right environments E^R (E^R_L = 1,
+ * E^R_{k-1} = sum_i X_k(i) E^R_k Y_k(i)^T).  Either gradient may be NULL.
+ * Environments in FP64.  Workspace: tt_inner_workspace_size.  Asynchronous. */
+int tt_inner_backward(const tt_train* x, const tt_train* y, double dout, tt_train* dx,
+                      tt_train* dy, void* workspace, size_t ws_bytes, void* stream);
+
+/* Device workspace (bytes) that tt_eval_backward needs for n samples.  Samples
+ * are processed in chunks of at most 16384, so the size stops growing beyond that. */
+size_t tt_eval_backward_workspace_size(const tt_train* x, int64_t n);
+
+/* dG_k[:, i, :] += sum_{s : i_k^s = i} dvalues_s prefix_s^T suffix_s, where
+ * prefix_s = G_1[:, i_1^s, :] ... G_{k-1}[:, i_{k-1}^s, :] and suffix_s is the
+ * product of the cores right of k.  Prefixes and suffixes and the per-site
+ * reduction over samples are FP64.  dvalues: device [n], x's dtype.  Asynchronous. */
+int tt_eval_backward(const tt_train* x, const uint8_t* digits, int64_t n, const void* dvalues,
+                     tt_train* dx, void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBTT_TT_H */

@@ -1,0 +1,144 @@
+// Shared device/host helpers of libtt (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tt.h"
+
+namespace tt {
+
+// ---------------------------------------------------------------- host errors
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define TT_CUDA_CHECK(expr)                                                             \
+  do {                                                                                  \
+    cudaError_t _e = (expr);                                                            \
+    if (_e != cudaSuccess)                                                              \
+      return ::tt::fail(TT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+#define TT_TRY(...)                 \
+  do {                              \
+    int _s = (__VA_ARGS__);         \
+    if (_s != TT_OK) return _s;     \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int num_sms();
+
+// ----------------------------------------------------------- device status word
+// Bit flags a kernel may raise; the host reads them at the next synchronisation.
+enum : unsigned {
+  ST_NONCONVERGED = 1u,  // Jacobi sweep cap reached
+  ST_TIMEOUT = 2u,       // bounded wait expired
+  ST_NONFINITE = 4u,     // NaN / Inf met
+  ST_BAD_INDEX = 8u      // an index argument was out of range (access skipped)
+};
+
+// ---------------------------------------------------------- warp reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Reduce-scatter of 32 values across a warp: on entry lane l holds partials v[0..31];
+// on exit v[0] of lane l holds the warp total of index l.  31 shuffles in all.
+template <typename T>
+__device__ __forceinline__ void warp_reduce_scatter32(T (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      T send = upper ? v[i] : v[i + off];
+      T keep = upper ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+}
+
+// Block-wide sum; every thread gets the total.  `scratch` holds >= 32 values.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  T t = (lane < nwarps) ? scratch[lane] : T(0);
+  t = warp_sum(t);
+  return t;
+}
+
+// ------------------------------------------------------- bounded grid barrier
+// Sense-reversing barrier for a cooperative launch (all CTAs co-resident).  Every
+// wait is bounded: after `limit` polls the CTA raises ST_TIMEOUT in *status and
+// returns false; callers then leave the kernel.  bar[0] = arrival count,
+// bar[1] = generation.  Both must be zero-initialised before the launch.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status,
+                                             long long limit = (1ll << 26)) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*vgen == gen) {
+        if (++polls > limit) {
+          atomicOr(status, (unsigned)ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        if ((polls & 1023) == 0 && (*(volatile unsigned*)status & ST_TIMEOUT)) {
+          ok = 0;  // another CTA gave up already
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+    if (*(volatile unsigned*)status & ST_TIMEOUT) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// --------------------------------------------------------------- small types
+
+template <typename T>
+struct DTypeOf;
+template <>
+struct DTypeOf<double> {
+  static constexpr int value = TT_F64;
+};
+template <>
+struct DTypeOf<float> {
+  static constexpr int value = TT_F32;
+};
+
+}  // namespace tt

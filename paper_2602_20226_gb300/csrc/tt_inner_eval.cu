@@ -1,0 +1,362 @@
+// TT inner product by the environment sweep, its adjoint, and batched evaluation.
+//
+// <x, y>: E_0 = 1, E_k = sum_i X_k(i)^T E_{k-1} Y_k(i) (r^x_k x r^y_k), accumulated in
+// FP64 for both dtypes.  Each site is two GEMMs: T = E_{k-1} Y_k (Y_k as
+// r^y_{k-1} x (d r^y_k)) and E_k = X_k'^T T' with X_k' = (r^x_{k-1} d) x r^x_k.
+//
+// Evaluation: each thread owns one sample and keeps its row vector
+// v = G_1[:, i_1, :] ... G_k[:, i_k, :] in shared memory (column-per-thread, so
+// accesses are conflict-free); the cores are read through the read-only cache
+// where a warp's lanes share at most d distinct rows per load.
+#include <vector>
+
+#include "tt_gemm.cuh"
+#include "tt_inner_eval.cuh"
+
+namespace tt {
+
+namespace {
+
+__global__ void set_scalar_kernel(double* p, double v) { *p = v; }
+
+// values[s] for samples [blockIdx.x * S, ...).  vbuf: two (rmax x S) planes of T.
+template <typename T, int JB>
+__global__ void eval_kernel(EvalParams<T> P, const uint8_t* __restrict__ digits, long long n,
+                            T* __restrict__ values, unsigned* status) {
+  extern __shared__ unsigned char smem_raw[];
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  const int S = blockDim.x;
+  const int tid = threadIdx.x;
+  const long long smp = (long long)blockIdx.x * S + tid;
+  const bool active = smp < n;
+  T* cur = buf;
+  T* nxt = buf + (size_t)P.rmax * S;
+  cur[tid] = T(1);
+  for (int k = 0; k < P.L; ++k) {
+    const int r0 = P.r[k], r1 = P.r[k + 1], d = P.d[k];
+    const T* G = P.g[k];
+    int dig = active ? (int)digits[smp * P.L + k] : 0;
+    if (dig >= d) {
+      if (status) atomicOr(status, (unsigned)ST_BAD_INDEX);
+      dig = 0;
+    }
+    for (int j0 = 0; j0 < r1; j0 += JB) {
+      T acc[JB];
+#pragma unroll
+      for (int t = 0; t < JB; ++t) acc[t] = T(0);
+      const int jn = min(JB, r1 - j0);
+      for (int a = 0; a < r0; ++a) {
+        const T v = cur[(size_t)a * S + tid];
+        const T* grow = G + ((long long)a * d + dig) * r1 + j0;
+#pragma unroll
+        for (int t = 0; t < JB; ++t)
+          if (t < jn) acc[t] = fma(v, __ldg(grow + t), acc[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < JB; ++t)
+        if (t < jn) nxt[(size_t)(j0 + t) * S + tid] = acc[t];
+    }
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  if (active) values[smp] = cur[tid];
+}
+
+// Backward of evaluation for one site k: dG_k[a, i, b] += sum_s w_s P_s[a] Sf_s[b] [i_k^s == i].
+// prefixes P (n x r0) and suffixes Sf (n x r1) are given row-major in FP64.
+template <typename T>
+__global__ void eval_bwd_site_kernel(const double* __restrict__ Pm, const double* __restrict__ Sm,
+                                     const T* __restrict__ w, const uint8_t* __restrict__ digits,
+                                     int L, int k, long long n, int r0, int d, int r1,
+                                     double* __restrict__ acc /* r0 x d x r1 */) {
+  // each CTA covers a chunk of samples and a tile of (a, b); accumulate then atomicAdd
+  const int a = blockIdx.y;
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long s0 = blockIdx.x * chunk, s1 = min(n, s0 + chunk);
+  for (int b = threadIdx.x; b < r1; b += blockDim.x) {
+    double loc[TT_MAX_MODE];
+    for (int i = 0; i < d; ++i) loc[i] = 0.0;
+    for (long long s = s0; s < s1; ++s) {
+      const int i = digits[s * L + k];
+      if (i < d) loc[i] += (double)w[s] * Pm[s * r0 + a] * Sm[s * r1 + b];
+    }
+    for (int i = 0; i < d; ++i)
+      if (loc[i] != 0.0) atomicAdd(acc + ((size_t)a * d + i) * r1 + b, loc[i]);
+  }
+}
+
+// prefix/suffix step:  out[s, :] = in[s, :] * G[:, i_s, :]   (prefix, left to right)
+//                      out[s, :] = G[:, i_s, :] * in[s, :]^T (suffix, right to left)
+template <typename T>
+__global__ void eval_step_kernel(const T* __restrict__ G, int r0, int d, int r1,
+                                 const uint8_t* __restrict__ digits, int L, int k, long long n,
+                                 const double* __restrict__ in, double* __restrict__ out,
+                                 bool suffix) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int rout = suffix ? r0 : r1;
+  if (e >= n * rout) return;
+  const long long s = e / rout;
+  const int j = (int)(e % rout);
+  int i = digits[s * L + k];
+  if (i >= d) i = 0;
+  double acc = 0.0;
+  if (!suffix) {
+    for (int a = 0; a < r0; ++a) acc += in[s * r0 + a] * (double)G[((long long)a * d + i) * r1 + j];
+  } else {
+    for (int b = 0; b < r1; ++b) acc += (double)G[((long long)j * d + i) * r1 + b] * in[s * r1 + b];
+  }
+  out[e] = acc;
+}
+
+__global__ void fill_ones_kernel(double* p, long long n) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < n) p[e] = 1.0;
+}
+
+template <typename T>
+__global__ void add_into_kernel(const double* src, long long n, T* dst) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < n) dst[e] += (T)src[e];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ inner
+size_t inner_workspace_bytes(const tt_train* x, const tt_train* y) {
+  int64_t env = 1, tb = 1, envsum = 0;
+  for (int k = 0; k <= x->L; ++k) {
+    env = std::max<int64_t>(env, x->ranks[k] * y->ranks[k]);
+    envsum += x->ranks[k] * y->ranks[k];
+  }
+  for (int k = 0; k < x->L; ++k) {
+    tb = std::max<int64_t>(tb, x->ranks[k] * (int64_t)x->d[k] * y->ranks[k + 1]);
+    tb = std::max<int64_t>(tb, y->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1]);
+  }
+  // forward: 2 env + 1 T; backward: all left envs + 2 right envs + 3 T buffers
+  return (size_t)(envsum + 2 * env + 3 * tb + 64) * sizeof(double) + 1024;
+}
+
+template <typename TX, typename TY>
+int inner_impl(const tt_train* x, const tt_train* y, double* out, void* ws, size_t ws_bytes,
+               cudaStream_t s) {
+  if (ws_bytes < inner_workspace_bytes(x, y)) return fail(TT_ERR_WORKSPACE, "tt_inner: workspace too small");
+  const int L = x->L;
+  int64_t env = 1, tb = 1;
+  for (int k = 0; k <= L; ++k) env = std::max<int64_t>(env, x->ranks[k] * y->ranks[k]);
+  for (int k = 0; k < L; ++k) tb = std::max<int64_t>(tb, x->ranks[k] * (int64_t)x->d[k] * y->ranks[k + 1]);
+  double* E = static_cast<double*>(ws);
+  double* E2 = E + env;
+  double* Tb = E2 + env;
+  set_scalar_kernel<<<1, 1, 0, s>>>(E, 1.0);
+  TT_CUDA_CHECK(cudaGetLastError());
+  for (int k = 0; k < L; ++k) {
+    const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
+    const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
+    const TX* X = static_cast<const TX*>(x->cores[k]);
+    const TY* Y = static_cast<const TY*>(y->cores[k]);
+    // T (rx0 x d ry1) = E (rx0 x ry0) Y (ry0 x d ry1)
+    TT_TRY((gemm<double, TY, double>(s, rx0, d * ry1, ry0, 1.0, E, ry0, 1, Y, (int64_t)d * ry1, 1,
+                                     0.0, Tb, (int64_t)d * ry1, 1)));
+    // E2 (rx1 x ry1) = X'^T ((rx1) x (rx0 d)) T' ((rx0 d) x ry1)
+    TT_TRY((gemm<TX, double, double>(s, rx1, ry1, rx0 * d, 1.0, X, 1, rx1, Tb, ry1, 1, 0.0, E2, ry1, 1)));
+    std::swap(E, E2);
+  }
+  TT_CUDA_CHECK(cudaMemcpyAsync(out, E, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TT_CUDA_CHECK(cudaStreamSynchronize(s));
+  return TT_OK;
+}
+
+template <typename TX, typename TY>
+int inner_backward_impl(const tt_train* x, const tt_train* y, double dout, tt_train* dx,
+                        tt_train* dy, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (ws_bytes < inner_workspace_bytes(x, y)) return fail(TT_ERR_WORKSPACE, "tt_inner_backward: workspace too small");
+  const int L = x->L;
+  int64_t env = 1, tb = 1;
+  std::vector<int64_t> eoff(L + 1);
+  int64_t off = 0;
+  for (int k = 0; k <= L; ++k) {
+    env = std::max<int64_t>(env, x->ranks[k] * y->ranks[k]);
+    eoff[k] = off;
+    off += x->ranks[k] * y->ranks[k];
+  }
+  for (int k = 0; k < L; ++k) {
+    tb = std::max<int64_t>(tb, x->ranks[k] * (int64_t)x->d[k] * y->ranks[k + 1]);
+    tb = std::max<int64_t>(tb, y->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1]);
+  }
+  double* EL = static_cast<double*>(ws);
+  double* ER = EL + off;
+  double* ER2 = ER + env;
+  double* T1 = ER2 + env;
+  double* T2 = T1 + tb;
+  double* T3 = T2 + tb;
+  // left environments E^L_0..E^L_{L-1}
+  set_scalar_kernel<<<1, 1, 0, s>>>(EL, 1.0);
+  TT_CUDA_CHECK(cudaGetLastError());
+  for (int k = 0; k < L - 1; ++k) {
+    const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
+    const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
+    const TX* X = static_cast<const TX*>(x->cores[k]);
+    const TY* Y = static_cast<const TY*>(y->cores[k]);
+    TT_TRY((gemm<double, TY, double>(s, rx0, d * ry1, ry0, 1.0, EL + eoff[k], ry0, 1, Y,
+                                     (int64_t)d * ry1, 1, 0.0, T1, (int64_t)d * ry1, 1)));
+    TT_TRY((gemm<TX, double, double>(s, rx1, ry1, rx0 * d, 1.0, X, 1, rx1, T1, ry1, 1, 0.0,
+                                     EL + eoff[k + 1], ry1, 1)));
+  }
+  set_scalar_kernel<<<1, 1, 0, s>>>(ER, 1.0);
+  TT_CUDA_CHECK(cudaGetLastError());
+  for (int k = L - 1; k >= 0; --k) {
+    const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
+    const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
+    const TX* X = static_cast<const TX*>(x->cores[k]);
+    const TY* Y = static_cast<const TY*>(y->cores[k]);
+    const double* El = EL + eoff[k];
+    if (dx && dx->cores[k]) {
+      // T1 = E^L Y ; dX' ((rx0 d) x rx1) += dout T1' ((rx0 d) x ry1) (E^R)^T (ry1 x rx1)
+      TT_TRY((gemm<double, TY, double>(s, rx0, d * ry1, ry0, 1.0, El, ry0, 1, Y, (int64_t)d * ry1, 1,
+                                       0.0, T1, (int64_t)d * ry1, 1)));
+      TT_TRY((gemm<double, double, TX>(s, rx0 * d, rx1, ry1, dout, T1, ry1, 1, ER, 1, ry1, 1.0,
+                                       static_cast<TX*>(dx->cores[k]), rx1, 1)));
+    }
+    if (dy && dy->cores[k]) {
+      // T2 = (E^L)^T X  (ry0 x d rx1) ; dY' ((ry0 d) x ry1) += dout T2' ((ry0 d) x rx1) E^R
+      TT_TRY((gemm<double, TX, double>(s, ry0, d * rx1, rx0, 1.0, El, 1, ry0, X, (int64_t)d * rx1, 1,
+                                       0.0, T2, (int64_t)d * rx1, 1)));
+      TT_TRY((gemm<double, double, TY>(s, ry0 * d, ry1, rx1, dout, T2, rx1, 1, ER, ry1, 1, 1.0,
+                                       static_cast<TY*>(dy->cores[k]), ry1, 1)));
+    }
+    if (k > 0) {
+      // T3 ((rx0 d) x ry1) = X' E^R ; E^R_new (rx0 x ry0) = T3'' (rx0 x d ry1) Y''^T
+      TT_TRY((gemm<TX, double, double>(s, rx0 * d, ry1, rx1, 1.0, X, rx1, 1, ER, ry1, 1, 0.0, T3, ry1, 1)));
+      TT_TRY((gemm<double, TY, double>(s, rx0, ry0, d * ry1, 1.0, T3, (int64_t)d * ry1, 1, Y, 1,
+                                       (int64_t)d * ry1, 0.0, ER2, ry0, 1)));
+      std::swap(ER, ER2);
+    }
+  }
+  return TT_OK;
+}
+
+// ------------------------------------------------------------------ eval
+template <typename T>
+int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values, cudaStream_t s,
+              unsigned* status_dev) {
+  if (n == 0) return TT_OK;
+  EvalParams<T> P;
+  P.L = x->L;
+  P.rmax = 1;
+  for (int k = 0; k < x->L; ++k) {
+    P.g[k] = static_cast<const T*>(x->cores[k]);
+    P.d[k] = x->d[k];
+    P.r[k] = (int)x->ranks[k];
+    P.rmax = std::max<int>(P.rmax, (int)x->ranks[k]);
+  }
+  P.r[x->L] = (int)x->ranks[x->L];
+  int S = 128;
+  auto smem_for = [&](int SS) { return 2 * (size_t)P.rmax * SS * sizeof(T); };
+  while (S > 32 && smem_for(S) > 200 * 1024) S /= 2;
+  if (smem_for(S) > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "tt_eval: rank too large");
+  static int configured[2] = {-1, -1};
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  const int which = sizeof(T) == 8 ? 0 : 1;
+  if (configured[which] != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(eval_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+    configured[which] = dev;
+  }
+  const long long blocks = ceil_div(n, S);
+  if (blocks > 0x7fffffffLL) return fail(TT_ERR_UNSUPPORTED, "tt_eval: too many samples");
+  eval_kernel<T, 8><<<(unsigned)blocks, S, smem_for(S), s>>>(P, digits, n, static_cast<T*>(values),
+                                                               status_dev);
+  TT_CUDA_CHECK(cudaGetLastError());
+  return TT_OK;
+}
+
+// Samples are processed in chunks so that the prefix store stays bounded.
+constexpr int64_t kEvalBwdChunk = 16384;
+
+size_t eval_backward_workspace_bytes(const tt_train* x, int64_t n) {
+  const int64_t c = std::max<int64_t>(1, std::min<int64_t>(n, kEvalBwdChunk));
+  int64_t rmax = 1, gmax = 1, pre = 0;
+  for (int k = 0; k <= x->L; ++k) {
+    rmax = std::max<int64_t>(rmax, x->ranks[k]);
+    pre += c * x->ranks[k];
+  }
+  for (int k = 0; k < x->L; ++k) gmax = std::max<int64_t>(gmax, x->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1]);
+  return (size_t)(pre + 2 * c * rmax + gmax + 64) * sizeof(double) + 1024;
+}
+
+template <typename T>
+int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, const void* dvalues,
+                       tt_train* dx, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (n == 0) return TT_OK;
+  if (ws_bytes < eval_backward_workspace_bytes(x, n))
+    return fail(TT_ERR_WORKSPACE, "tt_eval_backward: workspace too small");
+  const int L = x->L;
+  const int64_t chunk = std::min<int64_t>(n, kEvalBwdChunk);
+  int64_t rmax = 1;
+  for (int k = 0; k <= L; ++k) rmax = std::max<int64_t>(rmax, x->ranks[k]);
+  std::vector<int64_t> poff(L + 1);
+  int64_t off = 0;
+  for (int k = 0; k <= L; ++k) {
+    poff[k] = off;
+    off += chunk * x->ranks[k];
+  }
+  double* pre = static_cast<double*>(ws);
+  double* sA0 = pre + off;
+  double* sB0 = sA0 + chunk * rmax;
+  double* acc = sB0 + chunk * rmax;
+  const int TPB = 256;
+  for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+    const int64_t cn = std::min<int64_t>(chunk, n - c0);
+    const uint8_t* dg = digits + c0 * L;
+    const T* w = static_cast<const T*>(dvalues) + c0;
+    double* sA = sA0;
+    double* sB = sB0;
+    fill_ones_kernel<<<(unsigned)ceil_div(cn, TPB), TPB, 0, s>>>(pre, cn);
+    TT_CUDA_CHECK(cudaGetLastError());
+    for (int k = 0; k < L - 1; ++k) {
+      const int r0 = (int)x->ranks[k], r1 = (int)x->ranks[k + 1];
+      eval_step_kernel<T><<<(unsigned)ceil_div(cn * r1, TPB), TPB, 0, s>>>(
+          static_cast<const T*>(x->cores[k]), r0, x->d[k], r1, dg, L, k, cn, pre + poff[k],
+          pre + poff[k + 1], false);
+      TT_CUDA_CHECK(cudaGetLastError());
+    }
+    fill_ones_kernel<<<(unsigned)ceil_div(cn, TPB), TPB, 0, s>>>(sA, cn);
+    TT_CUDA_CHECK(cudaGetLastError());
+    for (int k = L - 1; k >= 0; --k) {
+      const int r0 = (int)x->ranks[k], r1 = (int)x->ranks[k + 1], d = x->d[k];
+      if (dx->cores[k]) {
+        const int64_t g = (int64_t)r0 * d * r1;
+        TT_CUDA_CHECK(cudaMemsetAsync(acc, 0, g * sizeof(double), s));
+        dim3 grid((unsigned)std::min<int64_t>(std::max<int64_t>(1, cn / 256), 256), (unsigned)r0);
+        eval_bwd_site_kernel<T><<<grid, 128, 0, s>>>(pre + poff[k], sA, w, dg, L, k, cn, r0, d, r1, acc);
+        TT_CUDA_CHECK(cudaGetLastError());
+        add_into_kernel<T><<<(unsigned)ceil_div(g, TPB), TPB, 0, s>>>(acc, g, static_cast<T*>(dx->cores[k]));
+        TT_CUDA_CHECK(cudaGetLastError());
+      }
+      if (k > 0) {
+        eval_step_kernel<T><<<(unsigned)ceil_div(cn * r0, TPB), TPB, 0, s>>>(
+            static_cast<const T*>(x->cores[k]), r0, d, r1, dg, L, k, cn, sA, sB, true);
+        TT_CUDA_CHECK(cudaGetLastError());
+        std::swap(sA, sB);
+      }
+    }
+  }
+  return TT_OK;
+}
+
+template int inner_impl<double, double>(const tt_train*, const tt_train*, double*, void*, size_t, cudaStream_t);
+template int inner_impl<float, float>(const tt_train*, const tt_train*, double*, void*, size_t, cudaStream_t);
+template int inner_backward_impl<double, double>(const tt_train*, const tt_train*, double, tt_train*,
+                                                 tt_train*, void*, size_t, cudaStream_t);
+template int inner_backward_impl<float, float>(const tt_train*, const tt_train*, double, tt_train*,
+                                               tt_train*, void*, size_t, cudaStream_t);
+template int eval_impl<double>(const tt_train*, const uint8_t*, int64_t, void*, cudaStream_t, unsigned*);
+template int eval_impl<float>(const tt_train*, const uint8_t*, int64_t, void*, cudaStream_t, unsigned*);
+template int eval_backward_impl<double>(const tt_train*, const uint8_t*, int64_t, const void*, tt_train*,
+                                        void*, size_t, cudaStream_t);
+template int eval_backward_impl<float>(const tt_train*, const uint8_t*, int64_t, const void*, tt_train*,
+                                       void*, size_t, cudaStream_t);
+
+}  // namespace tt

@@ -1,0 +1,90 @@
+// Launch descriptors and launchers of the core-by-core kernels.
+#pragma once
+
+#include <algorithm>
+
+#include "tt_common.cuh"
+
+namespace tt {
+
+template <typename T>
+struct ApplySite {
+  const T* w;
+  const T* g;
+  T* y;
+  int d, a0, a1, r0, r1;
+};
+template <typename T>
+struct ApplyParams {
+  int L;
+  long long row_start[TT_MAX_SITES + 1];  // warp rows (a, r, i) per site, prefix sums
+  ApplySite<T> site[TT_MAX_SITES];
+};
+
+template <typename T>
+struct HadamardSite {
+  const T* x;
+  const T* y;
+  T* z;
+  int d, r0, r1, s0, s1;
+};
+template <typename T>
+struct HadamardParams {
+  int L;
+  long long row_start[TT_MAX_SITES + 1];  // rows (r, s, i)
+  HadamardSite<T> site[TT_MAX_SITES];
+};
+
+template <typename T>
+struct ApplyBwdSite {
+  const T* w;
+  const T* g;
+  const T* dy;
+  T* dg;
+  T* dw;
+  int d, a0, a1, r0, r1;
+};
+template <typename T>
+struct ApplyBwdParams {
+  int L;
+  long long row_start[TT_MAX_SITES + 1];   // rows (r, j) of dG
+  long long wblk_start[TT_MAX_SITES + 1];  // CTAs (a, i, a') for dW
+  ApplyBwdSite<T> site[TT_MAX_SITES];
+};
+
+template <typename T>
+struct HadamardBwdSite {
+  const T* x;
+  const T* y;
+  const T* dz;
+  T* dx;
+  T* dy;
+  int d, r0, r1, s0, s1;
+};
+template <typename T>
+struct HadamardBwdParams {
+  int L;
+  long long xrow_start[TT_MAX_SITES + 1];  // rows (r, i, r') of dX
+  long long yrow_start[TT_MAX_SITES + 1];  // rows (s, i) of dY
+  HadamardBwdSite<T> site[TT_MAX_SITES];
+};
+
+template <typename T>
+int launch_apply(cudaStream_t s, const ApplyParams<T>& P);
+template <typename T>
+int launch_hadamard(cudaStream_t s, const HadamardParams<T>& P);
+template <typename T>
+int launch_apply_bwd(cudaStream_t s, const ApplyBwdParams<T>& P, bool want_x, bool want_w);
+template <typename T>
+int launch_hadamard_bwd(cudaStream_t s, const HadamardBwdParams<T>& P, bool want_x, bool want_y);
+
+template <typename T>
+int transpose_rm_to_cm(cudaStream_t s, const T* src, int m, int n, T* dst);
+template <typename T>
+int extract_r(cudaStream_t s, const T* A, int lda, int p, int n, T* R);
+template <typename T>
+int extract_rt(cudaStream_t s, const T* A, int lda, int p, int n, double* X);
+template <typename T>
+int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out);
+
+}  // namespace tt

@@ -1,0 +1,190 @@
+// Blocked Householder QR of a column-major m x n matrix (used by both rounding sweeps).
+//
+// Panel of nb columns: one CTA factors it column by column (Householder vector,
+// tau, and the upper-triangular T of the compact WY form I - V T V^T), reading the
+// panel from global memory.  For every column the dot products of the new
+// Householder vector with all other panel columns (the trailing-column update and
+// the column of T) come out of ONE block reduction: a 32-wide warp reduce-scatter
+// followed by a cross-warp sum in shared memory.
+//
+// Trailing update A <- (I - V T^T V^T) A and thin-Q formation
+// Q = H_1 ... H_p [I; 0] use three GEMMs per panel (W = V^T A, W <- T^(T) W, A -= V W).
+#include "tt_qr.cuh"
+
+namespace tt {
+
+namespace {
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda, int m, int j0,
+                                                      int jb, T* __restrict__ tau,
+                                                      T* __restrict__ Tm, int ldt,
+                                                      T* __restrict__ Vb, int ldv) {
+  constexpr int NW = NT / 32;
+  __shared__ T red[NW][33];
+  __shared__ T dvec[32];
+  __shared__ T Ts[32][33];
+  __shared__ T s_tau, s_scal;
+  __shared__ T s_sum[32];
+  __shared__ int s_nz;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < 32 * 33; e += NT) (&Ts[0][0])[e] = T(0);
+  __syncthreads();
+
+  for (int c = 0; c < jb; ++c) {
+    const int j = j0 + c;
+    T* colj = A + (int64_t)j * lda;
+    // ---- 1. norm of the part below the diagonal
+    T part = T(0);
+    for (int i = j + 1 + tid; i < m; i += NT) {
+      const T v = colj[i];
+      part += v * v;
+    }
+    const T s = block_sum(part, s_sum);
+    if (tid == 0) {
+      const T alpha = colj[j];
+      if (s == T(0)) {
+        s_tau = T(0);
+        s_scal = T(1);
+        s_nz = 0;
+      } else {
+        const T beta = -copysign(sqrt(alpha * alpha + s), alpha);
+        s_tau = (beta - alpha) / beta;
+        s_scal = T(1) / (alpha - beta);
+        colj[j] = beta;
+        s_nz = 1;
+      }
+    }
+    __syncthreads();
+    const T tj = s_tau;
+    if (s_nz) {
+      const T sc = s_scal;
+      for (int i = j + 1 + tid; i < m; i += NT) colj[i] *= sc;
+    }
+    __syncthreads();
+    // ---- 2. d_t = A[j, j0+t] + sum_{i>j} A[i, j] A[i, j0+t]  for every t != c
+    //      (t < c: v_t^T v_c for the T factor; t > c: v_c^T a_t for the update)
+    T acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = T(0);
+    for (int i = j + 1 + tid; i < m; i += NT) {
+      const T vi = colj[i];
+      const T* row = A + (int64_t)j0 * lda + i;
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < jb) acc[t] += vi * row[(int64_t)t * lda];
+    }
+    warp_reduce_scatter32(acc, lane);
+    red[warp][lane] = acc[0];
+    __syncthreads();
+    if (tid < 32) {
+      T d = T(0);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) d += red[w][tid];
+      if (tid < jb) d += A[(int64_t)(j0 + tid) * lda + j];
+      dvec[tid] = d;
+    }
+    __syncthreads();
+    // ---- 3. apply H_c to the remaining panel columns, and extend T
+    if (tj != T(0)) {
+      for (int t = c + 1; t < jb; ++t) {
+        const T f = tj * dvec[t];
+        T* colt = A + (int64_t)(j0 + t) * lda;
+        for (int i = j + 1 + tid; i < m; i += NT) colt[i] -= f * colj[i];
+      }
+      if (tid > c && tid < jb) A[(int64_t)(j0 + tid) * lda + j] -= tj * dvec[tid];
+    }
+    if (tid < c) {
+      T v = T(0);
+      for (int q = tid; q < c; ++q) v += Ts[tid][q] * dvec[q];
+      Ts[tid][c] = -tj * v;
+    }
+    if (tid == 0) {
+      Ts[c][c] = tj;
+      tau[j] = tj;
+    }
+    __syncthreads();
+  }
+  // explicit unit-lower-trapezoidal V (rows j0..m-1) and T to global
+  for (int t = 0; t < jb; ++t) {
+    const int jc = j0 + t;
+    const T* src = A + (int64_t)jc * lda;
+    T* dst = Vb + (int64_t)jc * ldv;
+    for (int i = j0 + tid; i < m; i += NT) dst[i] = (i < jc) ? T(0) : (i == jc ? T(1) : src[i]);
+  }
+  for (int e = tid; e < jb * jb; e += NT) {
+    const int r = e % jb, cc = e / jb;
+    Tm[r + (int64_t)cc * ldt] = Ts[r][cc];
+  }
+}
+
+template <typename T>
+__global__ void init_thin_q_kernel(T* Q, int m, int p, int ldq) {
+  const int64_t total = (int64_t)m * p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), c = (int)(e / m);
+    Q[i + (int64_t)c * ldq] = (i == c) ? T(1) : T(0);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
+  const int p = std::min(m, n);
+  const int nb = w.nb;
+  int panel = 0;
+  for (int j0 = 0; j0 < p; j0 += nb, ++panel) {
+    const int jb = std::min(nb, p - j0);
+    T* Tm = w.tmat + (int64_t)panel * nb * nb;
+    qr_panel_kernel<T, 512><<<1, 512, 0, s>>>(A, lda, m, j0, jb, w.tau, Tm, nb, w.vbuf, w.ldv);
+    TT_CUDA_CHECK(cudaGetLastError());
+    const int nt = n - (j0 + jb);
+    if (nt <= 0) continue;
+    const int mr = m - j0;
+    const T* V = w.vbuf + j0 + (int64_t)j0 * w.ldv;
+    T* At = A + j0 + (int64_t)(j0 + jb) * lda;
+    // W = V^T At   (jb x nt, column-major ld jb)
+    TT_TRY(gemm<T, T, T>(s, jb, nt, mr, 1.0, V, w.ldv, 1, At, 1, lda, 0.0, w.w1, 1, jb));
+    // W2 = T^T W
+    TT_TRY(gemm<T, T, T>(s, jb, nt, jb, 1.0, Tm, nb, 1, w.w1, 1, jb, 0.0, w.w2, 1, jb));
+    // At -= V W2
+    TT_TRY(gemm<T, T, T>(s, mr, nt, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, At, 1, lda));
+  }
+  w.m = m;
+  w.n = n;
+  w.npanels = panel;
+  return TT_OK;
+}
+
+template <typename T>
+int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq) {
+  const int m = w.m, p = std::min(w.m, w.n), nb = w.nb;
+  {
+    const int64_t total = (int64_t)m * p;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 8192));
+    init_thin_q_kernel<T><<<blocks, 256, 0, s>>>(Q, m, p, ldq);
+    TT_CUDA_CHECK(cudaGetLastError());
+  }
+  for (int panel = w.npanels - 1; panel >= 0; --panel) {
+    const int j0 = panel * nb;
+    const int jb = std::min(nb, p - j0);
+    const int mr = m - j0, nc = p - j0;
+    const T* V = w.vbuf + j0 + (int64_t)j0 * w.ldv;
+    const T* Tm = w.tmat + (int64_t)panel * nb * nb;
+    T* Qs = Q + j0 + (int64_t)j0 * ldq;
+    // W = V^T Qs ; W2 = T W ; Qs -= V W2
+    TT_TRY(gemm<T, T, T>(s, jb, nc, mr, 1.0, V, w.ldv, 1, Qs, 1, ldq, 0.0, w.w1, 1, jb));
+    TT_TRY(gemm<T, T, T>(s, jb, nc, jb, 1.0, Tm, 1, nb, w.w1, 1, jb, 0.0, w.w2, 1, jb));
+    TT_TRY(gemm<T, T, T>(s, mr, nc, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, Qs, 1, ldq));
+  }
+  return TT_OK;
+}
+
+template int householder_qr<double>(cudaStream_t, double*, int, int, int, QrWork<double>&);
+template int householder_qr<float>(cudaStream_t, float*, int, int, int, QrWork<float>&);
+template int form_thin_q<double>(cudaStream_t, const QrWork<double>&, double*, int);
+template int form_thin_q<float>(cudaStream_t, const QrWork<float>&, float*, int);
+
+}  // namespace tt

@@ -1,0 +1,32 @@
+// Householder QR used by the rounding sweeps.
+#pragma once
+
+#include "tt_common.cuh"
+#include "tt_gemm.cuh"
+
+namespace tt {
+
+// Scratch of one QR (all device memory, carved from the caller's workspace).
+template <typename T>
+struct QrWork {
+  int nb = 16;       // panel width (<= 32)
+  T* tau = nullptr;  // [>= min(m, n)]
+  T* tmat = nullptr; // [npanels][nb][nb] T factors (column-major)
+  T* vbuf = nullptr; // explicit Householder vectors, column-major, ld = ldv >= m
+  int ldv = 0;
+  T* w1 = nullptr;   // [nb * ncols]
+  T* w2 = nullptr;   // [nb * ncols]
+  // filled by householder_qr
+  int m = 0, n = 0, npanels = 0;
+};
+
+// In-place QR of the column-major m x n matrix A (ld lda): on return the upper
+// trapezoid holds R (min(m,n) x n) and w holds the reflectors.
+template <typename T>
+int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w);
+
+// Thin Q (m x min(m,n), column-major, ld ldq) from the reflectors of the last QR.
+template <typename T>
+int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq);
+
+}  // namespace tt

@@ -1,0 +1,35 @@
+// FP64 bond SVD (one-sided Jacobi) and truncation used by tt_round.
+#pragma once
+
+#include "tt_common.cuh"
+
+namespace tt {
+
+struct SvdWork {
+  static constexpr int kMaxSweeps = 40;
+  double* X = nullptr;  // n x p, column-major (X = R^T), ld ldx
+  int ldx = 0;
+  double* V = nullptr;  // p x p, column-major, ld ldv
+  int ldv = 0;
+  double* sigma = nullptr;  // [p] sorted descending
+  int* perm = nullptr;      // [p] column of sigma_sorted[t]
+  int* rank = nullptr;      // device int: truncated rank
+  unsigned* bar = nullptr;  // [2] grid barrier state
+  unsigned* rot = nullptr;  // [kMaxSweeps] rotations per sweep
+  unsigned* status = nullptr;
+  int* sweeps = nullptr;
+  double* norm = nullptr;   // device double ||x||
+};
+
+// One-sided Jacobi on the columns of X (nrow x ncol); V accumulates the rotations.
+int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps);
+
+// sigma, perm and the truncation rank with delta = delta_scale * (*norm).
+int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
+                 int64_t max_rank);
+
+// Vsel (ncol x r, column-major) = V[:, perm[:r]];  F (r x nrow, row-major) = X[:, perm[:r]]^T.
+template <typename TO>
+int svd_gather(cudaStream_t s, const SvdWork& w, int nrow, int ncol, int r, TO* Vsel, TO* F);
+
+}  // namespace tt

@@ -1,0 +1,106 @@
+"""Host-side checks that need no GPU: the C ABI library loads and exports every
+declared entry point, the host constructors agree with the oracle's, and the
+seeded inputs are deterministic."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import core, structured
+from paper_2602_20226_gb300 import _abi, inputs, qtt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    txt = open(os.path.join(ROOT, "include", "tt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(tt_[a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _header_functions()
+    for want in ["tt_apply_mpo", "tt_hadamard", "tt_round", "tt_inner", "tt_eval",
+                 "tt_apply_mpo_backward", "tt_hadamard_backward", "tt_inner_backward",
+                 "tt_eval_backward", "tt_last_error"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    if not os.path.exists(_abi.LIB_PATH):
+        from paper_2602_20226_gb300 import build
+
+        build.build()
+    lib = ctypes.CDLL(_abi.LIB_PATH)
+    for name in _header_functions():
+        assert hasattr(lib, name), name
+    # the binding declares a signature for every header function
+    assert set(_header_functions()) <= set(_abi.exported_symbols())
+
+
+def test_library_validates_on_host_without_gpu():
+    """Argument validation runs before any CUDA call, so it works on a CPU-only host."""
+    lib = _abi.load()
+    assert lib.tt_apply_mpo(None, None, None, None) == 1  # TT_ERR_ARG
+    assert b"NULL" in lib.tt_last_error()
+    L = 3
+    d = (ctypes.c_int32 * L)(2, 2, 2)
+    r = (ctypes.c_int64 * (L + 1))(1, 4, 4, 2)  # bad boundary rank
+    p = (ctypes.c_void_p * L)(1, 2, 3)
+    x = _abi.tt_train(L, _abi.TT_F64, d, r, p)
+    assert lib.tt_eval(ctypes.byref(x), None, 0, None, None) == 2  # TT_ERR_SHAPE
+    r2 = (ctypes.c_int64 * (L + 1))(1, 4, 4, 1)
+    x2 = _abi.tt_train(L, 7, d, r2, p)
+    assert lib.tt_eval(ctypes.byref(x2), None, 0, None, None) == 3  # TT_ERR_DTYPE
+    x3 = _abi.tt_train(200, _abi.TT_F64, d, r2, p)
+    assert lib.tt_eval(ctypes.byref(x3), None, 0, None, None) == 4  # TT_ERR_UNSUPPORTED
+    x4 = _abi.tt_train(L, _abi.TT_F32, d, r2, p)
+    out = _abi.tt_train(L, _abi.TT_F32, d, (ctypes.c_int64 * (L + 1))(1, 4, 4, 1), p)
+    # FP64 form on FP32 cores is a dtype error, caught before any launch
+    assert lib.tt_round(ctypes.byref(x4), 1e-6, 0, _abi.TT_PREC_FP64, ctypes.byref(out), None,
+                        ctypes.c_void_p(1), 1 << 20, None) == 3
+    assert lib.tt_round(ctypes.byref(x4), -1.0, 0, _abi.TT_PREC_MIXED, ctypes.byref(out), None,
+                        ctypes.c_void_p(1), 1 << 20, None) == 1
+    assert lib.tt_round_workspace_size(ctypes.byref(x2), 0) == 0
+
+
+@pytest.mark.parametrize("n_dims,bits", [(1, 7), (2, 4), (3, 3), (2, 5)])
+def test_laplacian_constructor_matches_oracle(n_dims, bits):
+    a = qtt.laplacian_mpo(n_dims, bits)
+    b = structured.laplacian_mpo(n_dims, bits)
+    assert core.ranks(a) == core.ranks(b)
+    assert np.array_equal(core.full_mpo(a), core.full_mpo(b))
+
+
+@pytest.mark.parametrize("fn", ["exp", "cos", "sin"])
+def test_closed_form_constructors_match_oracle(fn):
+    bits = 9
+    if fn == "exp":
+        a = qtt.exp_tt(bits, -1.0, 2.0, 0.7, 0.3)
+        b = structured.exp_tt([2] * bits, -1.0, 2.0, 0.7, 0.3)
+    elif fn == "cos":
+        a = qtt.cos_tt(bits, -1.0, 1.0, 5.0, 0.2)
+        b = structured.cos_tt([2] * bits, -1.0, 1.0, 5.0, 0.2)
+    else:
+        a = qtt.sin_tt(bits, 0.0, 1.0, 2 * np.pi)
+        b = structured.sin_tt([2] * bits, 0.0, 1.0, 2 * np.pi)
+    assert np.allclose(core.full(a), core.full(b), rtol=1e-14, atol=1e-14)
+
+
+def test_inputs_are_deterministic():
+    a = inputs.random_tt(5, 6, 2, 4)
+    b = inputs.random_tt(5, 6, 2, 4)
+    assert all(np.array_equal(u, v) for u, v in zip(a, b))
+    assert [c.shape for c in a] == [(1, 2, 4)] + [(4, 2, 4)] * 4 + [(4, 2, 1)]
+    s = inputs.batch_shapes(1, 64)
+    assert all(20 <= L <= 60 and 8 <= r <= 128 and a in (3, 4, 5) for L, r, a in s)
+    dg = inputs.random_digits(3, 1000, [2, 3, 5])
+    assert dg.dtype == np.uint8 and dg[:, 2].max() == 4 and dg[:, 1].max() == 2
+
+
+def test_random_tt_norm_is_one_in_expectation():
+    norms = [core.norm(inputs.random_tt(s, 8, 2, 4)) ** 2 for s in range(200)]
+    assert 0.8 < np.mean(norms) < 1.25
