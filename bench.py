@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the quantics-TT apply + round hot path on GB300.
+
+One step = y = W x (MPO apply) followed by y' = round(y, eps) on one TT, all through
+the libtt C ABI.  Default workload: 2D quantics TT, 2 x 20 bits interleaved (L = 40),
+d = 2, rank 64 (seeded Gaussian cores), the 2D Dirichlet Laplacian MPO (rank 5,
+pre-round rank 320), eps = 1e-8, the plain FP64 form.  Alongside, the same step in the
+mixed form (FP32 cores, tensor-core GEMMs, FP64 bond SVDs), its speed-up over FP64 and
+its error against the FP64 oracle.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (a single TT's sweeps are a
+sequential chain: replicas only); the reported value is the sum over ranks of the
+work done divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPO·TT apply+round GFLOP/s & % tensor peak, mixed vs FP64 GPU, rel err ≤1e-6"
+WORKLOAD = {
+    "workload": "2D quantics TT L=40 (2x20 bits interleaved), d=2, rank 64, 2D Dirichlet Laplacian "
+                "MPO rank 5 (n=320), apply + tt_round eps=1e-8",
+    "L": 40, "bits": 20, "n_dims": 2, "rank": 64, "mpo_rank": 5, "eps": 1e-8, "seed": 2,
+}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 ALU peak of GB300, derived from its unit count and clock: 152 SMs x 2 DFMA per
+# clock per SM x 2 flops x 2.07 GHz = 1.26 TFLOP/s (a DFMA-loop microbenchmark measured
+# 1.19 TFLOP/s at 2070 MHz).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def build_inputs(dtype):
+    from paper_2602_20226_gb300 import inputs, qtt
+
+    w = WORKLOAD
+    x = inputs.random_tt(w["seed"], w["L"], 2, w["rank"])
+    W = qtt.laplacian_mpo(w["n_dims"], w["bits"])
+    if dtype == "f32":
+        x = [c.astype(np.float32) for c in x]
+        W = [c.astype(np.float32) for c in W]
+    return x, W
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2602_20226_gb300 as tt
+    from paper_2602_20226_gb300 import _abi
+    from paper_2602_20226_gb300.flops import apply_flops, round_flops
+
+    rank, world, local = _dist()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    lib = tt.load()
+    eps = WORKLOAD["eps"]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def make(dtype):
+        x_np, W_np = build_inputs(dtype)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        X = tt.TT.from_numpy(x_np, device=dev, dtype=tdt)
+        W = tt.MPO.from_numpy(W_np, device=dev, dtype=tdt)
+        Y0 = tt.tt_apply_mpo(W, X)
+        ws = torch.empty(tt.tt_round_workspace_size(Y0, tt.TT_PREC_FP64 if dtype == "f64" else tt.TT_PREC_MIXED),
+                         dtype=torch.uint8, device=dev)
+        bufs = [torch.empty(c.numel(), dtype=tdt, device=dev) for c in Y0.cores]
+        return x_np, W_np, X, W, ws, bufs
+
+    def step(X, W, ws, bufs, prec):
+        Y = tt.tt_apply_mpo(W, X)
+        Z, _ = tt.tt_round(Y, eps, 0, prec, workspace=ws, out_buffers=bufs)
+        return Y, Z
+
+    def timed(X, W, ws, bufs, prec, K, Wm):
+        for _ in range(Wm):
+            step(X, W, ws, bufs, prec)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        l0 = lib.tt_launch_count()
+        ms_steps = []
+        t0 = time.perf_counter()
+        for _ in range(K):
+            flush.zero_()  # L2 flush, outside the event-timed region
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Y, Z = step(X, W, ws, bufs, prec)
+            e1.record(stream)
+            e1.synchronize()
+            ms_steps.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        launches = int(lib.tt_launch_count() - l0)
+        return Y, Z, ms_steps, wall, launches
+
+    K, Wm = args.steps, args.warmup
+    # ---- FP64 form (the reported value)
+    x_np, W_np, X, W, ws, bufs = make("f64")
+    with ClockSampler(dev.index or 0) as clk:
+        Y, Z, ms64, wall64, launches = timed(X, W, ws, bufs, tt.TT_PREC_FP64, K, Wm)
+    clocks = clk.summary()
+    ms_step = float(np.mean(ms64))
+    fl_apply = apply_flops([int(v) for v in W.ranks], X.ranks, X.dims)
+    fl_round = round_flops(Y.ranks, Z.ranks, X.dims)
+    flops_step = fl_apply + fl_round["total"]
+
+    # ---- dominant kernel and its live event timing (one profiled step, same stream)
+    lib.tt_profile_enable(1)
+    step(X, W, ws, bufs, tt.TT_PREC_FP64)
+    torch.cuda.synchronize(dev)
+    prof = {}
+    import ctypes
+    for cls, name in [(0, "jacobi_svd"), (1, "householder_qr"), (2, "core_gemm")]:
+        ms_c, fl_c, n_c = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        lib.tt_profile_read(cls, ctypes.byref(ms_c), ctypes.byref(fl_c), ctypes.byref(n_c))
+        prof[name] = {"ms": ms_c.value, "nominal_flops": fl_c.value, "launches": int(n_c.value)}
+    lib.tt_profile_enable(0)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved_tflops = d["nominal_flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+    roofline = {
+        "kernel": dom,
+        "bound": "alu",
+        "achieved": round(achieved_tflops, 6),
+        "peak": round(FP64_PEAK_TFLOPS, 4),
+        "unit": "TFLOP/s",
+        "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 6),
+        "traffic": None,
+        "peak_source": "derived FP64 ALU peak (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)",
+        "share_of_step": round(d["ms"] / max(ms_step, 1e-9), 4),
+        "launch_ms_avg": round(d["ms"] / max(d["launches"], 1), 4),
+        "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                       "tflops": round(v["nominal_flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+                   for k, v in prof.items()},
+    }
+
+    # ---- mixed form on the same TT shape (FP32 cores)
+    x32, W32, X32, Wd32, ws32, bufs32 = make("f32")
+    Y32, Z32, ms32, _, _ = timed(X32, Wd32, ws32, bufs32, tt.TT_PREC_MIXED, K, Wm)
+    ms_mixed = float(np.mean(ms32))
+
+    # ---- end to end: pinned host cores in, rounded cores out, through the public API
+    xh = [torch.as_tensor(c).pin_memory() for c in x_np]
+    wh = [torch.as_tensor(c).pin_memory() for c in W_np]
+    h2d = sum(t.numel() * t.element_size() for t in xh + wh)
+    e2e_ms, d2h = [], 0
+    for it in range(Wm + K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Xd = tt.TT([t.to(dev, non_blocking=True) for t in xh])
+        Wdd = tt.MPO([t.to(dev, non_blocking=True) for t in wh])
+        Yd = tt.tt_apply_mpo(Wdd, Xd)
+        Zd, _ = tt.tt_round(Yd, eps, 0, tt.TT_PREC_FP64, workspace=ws, out_buffers=bufs)
+        outs = [c.to("cpu") for c in Zd.cores]
+        e1.record(stream)
+        e1.synchronize()
+        if it >= Wm:
+            e2e_ms.append(e0.elapsed_time(e1))
+            d2h = sum(o.numel() * o.element_size() for o in outs)
+
+    # ---- aggregate over ranks (replicas)
+    t_max = ms_step
+    if world > 1:
+        tt_ = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tt_, op=dist.ReduceOp.MAX)
+        t_max = float(tt_.item())
+    value = world * flops_step / (t_max * 1e-3) / 1e9
+    value_mixed = flops_step / (ms_mixed * 1e-3) / 1e9
+    e2e_val = world * flops_step / (float(np.mean(e2e_ms)) * 1e-3) / 1e9
+
+    err_mixed = None
+    cpu = None
+    if rank == 0:
+        from oracle import core as ocore
+
+        # accuracy of the mixed form against the FP64 oracle on the same FP32 inputs
+        y32 = [c.astype(np.float64) for c in Y32.numpy()]
+        ref32 = ocore.round_tt(y32, eps)
+        err_mixed = ocore.rel_err(Z32.numpy(), ref32)
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(x_np, W_np, eps, flops_step)
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": K, "warmup": Wm, "ms_per_step": round(t_max, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, form="fp64", l2="flushed between steps (512 MB write, untimed)",
+                           parallelism=f"replicas x{world}"),
+            "nominal_flops_per_step": flops_step,
+            "round_flops": fl_round, "apply_flops": fl_apply,
+            "ranks_out_max": max(Z.ranks),
+            "mixed": {"value": round(value_mixed, 4), "unit": "GFLOP/s", "ms_per_step": round(ms_mixed, 4),
+                      "dtype": "f32 cores, 3xTF32 tensor-core GEMMs, FP64 bond SVD",
+                      "speedup_vs_fp64": round(ms_step / ms_mixed, 3),
+                      "rel_err_vs_fp64_oracle": err_mixed},
+            "roofline": roofline,
+            "e2e": {"value": round(e2e_val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(float(np.mean(e2e_ms)), 4)},
+            "gpu_launches": launches,
+            "gpu_launches_per_step": launches // max(K, 1),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "wall_s_timed_region": round(wall64, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(x_np, W_np, eps, flops_step, repeats=2):
+    """The FP64 oracle (numpy + LAPACK) on the host cores: full apply + round steps."""
+    from oracle import core as ocore
+    from oracle import structured
+
+    W = structured.laplacian_mpo(WORKLOAD["n_dims"], WORKLOAD["bits"])
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        y = ocore.apply_mpo(W, [c.astype(np.float64) for c in x_np])
+        ocore.round_tt(y, eps)
+        times.append(time.perf_counter() - t0)
+    s = float(np.mean(times))
+    return {"value": round(flops_step / s / 1e9, 4), "unit": "GFLOP/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": f"{repeats} full steps (apply + round of the L=40 rank-64 TT), "
+                                        f"{s:.2f} s each, numpy/LAPACK FP64"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: timed on the host cores, same workload and metric."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import core as ocore
+    from oracle import structured
+    from paper_2602_20226_gb300.flops import apply_flops, round_flops
+
+    x_np, _ = build_inputs("f64")
+    W = structured.laplacian_mpo(WORKLOAD["n_dims"], WORKLOAD["bits"])
+    eps = WORKLOAD["eps"]
+    y = ocore.apply_mpo(W, x_np)
+    z = ocore.round_tt(y, eps)
+    flops = apply_flops(ocore.ranks(W), ocore.ranks(x_np), ocore.dims(x_np)) + \
+        round_flops(ocore.ranks(y), ocore.ranks(z), ocore.dims(x_np))["total"]
+    for _ in range(args.warmup):
+        ocore.round_tt(ocore.apply_mpo(W, x_np), eps)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ocore.round_tt(ocore.apply_mpo(W, x_np), eps)
+        ts.append(time.perf_counter() - t0)
+    ms = float(np.mean(ts)) * 1e3
+    val = flops / (ms * 1e-3) / 1e9
+    cores = len(os.sched_getaffinity(0))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, form="fp64 oracle (numpy/LAPACK, host cores)"),
+        "cpu_baseline": {"value": round(val, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step is one full apply + round of the workload"},
+        "e2e": {"value": round(val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,35 @@ size_t tt_eval_backward_workspace_size(const tt_train* x, int64_t n);
 int tt_eval_backward(const tt_train* x, const uint8_t* digits, int64_t n, const void* dvalues,
                      tt_train* dx, void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- diagnostics ---- */
+
+/* Number of CUDA kernels this library has launched in this process so far (all
+ * threads, all devices).  A caller reads it before and after a region of work to
+ * count the launches inside it. */
+uint64_t tt_launch_count(void);
+
+/* Event profiler of tt_round.  tt_profile_enable(1) clears the counters and turns it
+ * on (0 turns it off).  While on, tt_round brackets each phase with a pair of CUDA
+ * events on its own stream and accumulates, per class, the elapsed time, the nominal
+ * flops of the phase and the number of phases:
+ *   class 0  Jacobi SVD launches (12 p^3 flops each for a p x p factor)
+ *   class 1  Householder QR with thin Q (4 m n^2 - 4 n^3 / 3)
+ *   class 2  the GEMMs that form the new cores (2 m n k)
+ * tt_profile_read returns TT_ERR_ARG for an unknown class. */
+void tt_profile_enable(int32_t on);
+int tt_profile_read(int32_t cls, double* ms, double* nominal_flops, uint64_t* count);
+
+/* C = alpha A B + beta C in FP32 on the tensor cores: TF32 with a 3-term hi/lo split
+ * (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation), the dense-GEMM kernel the
+ * mixed form of tt_round uses.  No counterpart in the paper; exported so that the
+ * tensor-core kernel can be tested and timed on its own.
+ * Element (m, k) of A is A[m*sam + k*sak], (k, n) of B is B[k*sbk + n*sbn], (m, n) of
+ * C is C[m*scm + n*scn] (device pointers; any strides).  beta = 0 never reads C.
+ * Asynchronous. */
+int tt_gemm_f32(int32_t M, int32_t N, int32_t K, double alpha, const float* A, int64_t sam,
+                int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
+                int64_t scm, int64_t scn, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

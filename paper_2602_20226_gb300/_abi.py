@@ -52,6 +52,9 @@ i32, i64, f64, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_si
 SIGNATURES = {
     "tt_last_error": (ctypes.c_char_p, []),
     "tt_version": (ctypes.c_char_p, []),
+    "tt_launch_count": (ctypes.c_uint64, []),
+    "tt_profile_enable": (None, [i32]),
+    "tt_profile_read": (ctypes.c_int, [i32, P(f64), P(f64), P(ctypes.c_uint64)]),
     "tt_apply_mpo": (ctypes.c_int, [P(tt_mpo), P(tt_train), P(tt_train), vp]),
     "tt_hadamard": (ctypes.c_int, [P(tt_train), P(tt_train), P(tt_train), vp]),
     "tt_round_workspace_size": (sz, [P(tt_train), i32]),
@@ -64,6 +67,7 @@ SIGNATURES = {
     "tt_inner_backward": (ctypes.c_int, [P(tt_train), P(tt_train), f64, P(tt_train), P(tt_train), vp, sz, vp]),
     "tt_eval_backward_workspace_size": (sz, [P(tt_train), i64]),
     "tt_eval_backward": (ctypes.c_int, [P(tt_train), vp, i64, vp, P(tt_train), vp, sz, vp]),
+    "tt_gemm_f32": (ctypes.c_int, [i32, i32, i32, f64, vp, i64, i64, vp, i64, i64, f64, vp, i64, i64, vp]),
 }
 
 _lib = None

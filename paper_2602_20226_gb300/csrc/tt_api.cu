@@ -1,12 +1,15 @@
 // C ABI of libtt: host-side validation, dispatch by dtype, error plumbing.
 // Nothing is enqueued before all arguments have been checked.  No exception leaves
 // an entry point.
+#include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <exception>
 #include <string>
 #include <vector>
 
+#include "tt_gemm.cuh"
 #include "tt_inner_eval.cuh"
 #include "tt_kernels.cuh"
 #include "tt_round.cuh"
@@ -15,6 +18,26 @@ namespace tt {
 
 namespace {
 thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+double g_prof_ms[PROF_CLASSES] = {0}, g_prof_flops[PROF_CLASSES] = {0};
+uint64_t g_prof_n[PROF_CLASSES] = {0};
+}  // namespace
+
+bool profile_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
+
+void profile_add(int cls, double ms, double flops) {
+  if (cls < 0 || cls >= PROF_CLASSES) return;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof_ms[cls] += ms;
+  g_prof_flops[cls] += flops;
+  g_prof_n[cls] += 1;
 }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -217,6 +240,23 @@ const char* tt_last_error(void) { return g_last_error.c_str(); }
 
 const char* tt_version(void) { return "libtt 0.1 (sm_103a)"; }
 
+uint64_t tt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void tt_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (int c = 0; c < PROF_CLASSES; ++c) g_prof_ms[c] = g_prof_flops[c] = 0.0, g_prof_n[c] = 0;
+  g_prof_on.store(on != 0);
+}
+
+int tt_profile_read(int32_t cls, double* ms, double* nominal_flops, uint64_t* count) {
+  if (cls < 0 || cls >= PROF_CLASSES) return fail(TT_ERR_ARG, "tt_profile_read: bad class");
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (ms) *ms = g_prof_ms[cls];
+  if (nominal_flops) *nominal_flops = g_prof_flops[cls];
+  if (count) *count = g_prof_n[cls];
+  return TT_OK;
+}
+
 int tt_apply_mpo(const tt_mpo* W, const tt_train* x, tt_train* y, void* stream) {
   return guarded([&]() -> int {
     TT_TRY(check_train(x, "x"));
@@ -385,6 +425,18 @@ int tt_eval_backward(const tt_train* x, const uint8_t* digits, int64_t n, const 
     return x->dtype == TT_F64
                ? eval_backward_impl<double>(x, digits, n, dvalues, dx, workspace, ws_bytes, as_stream(stream))
                : eval_backward_impl<float>(x, digits, n, dvalues, dx, workspace, ws_bytes, as_stream(stream));
+  });
+}
+
+int tt_gemm_f32(int32_t M, int32_t N, int32_t K, double alpha, const float* A, int64_t sam,
+                int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
+                int64_t scm, int64_t scn, void* stream) {
+  return guarded([&]() -> int {
+    if (M < 0 || N < 0 || K < 0) return fail(TT_ERR_ARG, "tt_gemm_f32: negative size");
+    if ((M > 0 && N > 0) && (!C || (K > 0 && (!A || !B)))) return fail(TT_ERR_ARG, "tt_gemm_f32: NULL operand");
+    g_last_error.clear();
+    return gemm_tf32x3(as_stream(stream), M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn,
+                       nullptr);
   });
 }
 

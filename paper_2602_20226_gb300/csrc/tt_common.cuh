@@ -14,12 +14,25 @@ namespace tt {
 
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+void note_launch();  // counts kernel launches made by the library (tt_launch_count)
+
+// opt-in event profiler of tt_round's phases (tt_profile_enable / tt_profile_read)
+enum ProfClass { PROF_JACOBI = 0, PROF_QR = 1, PROF_GEMM = 2, PROF_CLASSES = 3 };
+bool profile_enabled();
+void profile_add(int cls, double ms, double flops);
 
 #define TT_CUDA_CHECK(expr)                                                             \
   do {                                                                                  \
     cudaError_t _e = (expr);                                                            \
     if (_e != cudaSuccess)                                                              \
       return ::tt::fail(TT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// after a <<<...>>> launch: count it and check the launch error
+#define TT_LAUNCH_CHECK()                    \
+  do {                                       \
+    ::tt::note_launch();                     \
+    TT_CUDA_CHECK(cudaGetLastError());       \
   } while (0)
 
 #define TT_TRY(...)                 \

@@ -212,6 +212,17 @@ __global__ void extract_r_kernel(const T* A, int lda, int p, int n, T* R) {
   }
 }
 
+// X = R (p x n, column-major, FP64, zeros below the diagonal) from the QR'd A (ld lda)
+template <typename T>
+__global__ void extract_r_f64_kernel(const T* A, int lda, int p, int n, double* X) {
+  const long long total = (long long)p * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % p), c = (int)(e / p);
+    X[e] = (i <= c) ? (double)A[i + (long long)c * lda] : 0.0;
+  }
+}
+
 // X = R^T (n x p, column-major, FP64) from the QR'd A (ld lda)
 template <typename T>
 __global__ void extract_rt_kernel(const T* A, int lda, int p, int n, double* X) {
@@ -247,7 +258,7 @@ int launch_apply(cudaStream_t s, const ApplyParams<T>& P) {
   if (rows == 0) return TT_OK;
   if (ceil_div(rows, 8) > 0x7fffffffLL) return fail(TT_ERR_UNSUPPORTED, "apply: too many rows");
   apply_kernel<T><<<(unsigned)ceil_div(rows, 8), 256, 0, s>>>(P);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
@@ -257,7 +268,7 @@ int launch_hadamard(cudaStream_t s, const HadamardParams<T>& P) {
   if (rows == 0) return TT_OK;
   if (ceil_div(rows, 8) > 0x7fffffffLL) return fail(TT_ERR_UNSUPPORTED, "hadamard: too many rows");
   hadamard_kernel<T><<<(unsigned)ceil_div(rows, 8), 256, 0, s>>>(P);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
@@ -265,11 +276,11 @@ template <typename T>
 int launch_apply_bwd(cudaStream_t s, const ApplyBwdParams<T>& P, bool want_x, bool want_w) {
   if (want_x && P.row_start[P.L] > 0) {
     apply_bwd_x_kernel<T><<<(unsigned)ceil_div(P.row_start[P.L], 8), 256, 0, s>>>(P);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
   }
   if (want_w && P.wblk_start[P.L] > 0) {
     apply_bwd_w_kernel<T><<<(unsigned)P.wblk_start[P.L], 256, 0, s>>>(P);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
   }
   return TT_OK;
 }
@@ -278,11 +289,11 @@ template <typename T>
 int launch_hadamard_bwd(cudaStream_t s, const HadamardBwdParams<T>& P, bool want_x, bool want_y) {
   if (want_x && P.xrow_start[P.L] > 0) {
     hadamard_bwd_x_kernel<T><<<(unsigned)ceil_div(P.xrow_start[P.L], 8), 256, 0, s>>>(P);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
   }
   if (want_y && P.yrow_start[P.L] > 0) {
     hadamard_bwd_y_kernel<T><<<(unsigned)ceil_div(P.yrow_start[P.L], 8), 256, 0, s>>>(P);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
   }
   return TT_OK;
 }
@@ -292,28 +303,35 @@ int transpose_rm_to_cm(cudaStream_t s, const T* src, int m, int n, T* dst) {
   if (m <= 0 || n <= 0) return TT_OK;
   dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(m, 32));
   transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(src, m, n, dst);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
 template <typename T>
 int extract_r(cudaStream_t s, const T* A, int lda, int p, int n, T* R) {
   extract_r_kernel<T><<<grid_for((long long)p * n, 256, 4096), 256, 0, s>>>(A, lda, p, n, R);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+template <typename T>
+int extract_r_f64(cudaStream_t s, const T* A, int lda, int p, int n, double* X) {
+  extract_r_f64_kernel<T><<<grid_for((long long)p * n, 256, 4096), 256, 0, s>>>(A, lda, p, n, X);
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
 template <typename T>
 int extract_rt(cudaStream_t s, const T* A, int lda, int p, int n, double* X) {
   extract_rt_kernel<T><<<grid_for((long long)p * n, 256, 4096), 256, 0, s>>>(A, lda, p, n, X);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
 template <typename T>
 int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out) {
   sumsq_kernel<T><<<1, 1024, 0, s>>>(a, n, out);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
@@ -325,6 +343,7 @@ int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out) {
   template int transpose_rm_to_cm<T>(cudaStream_t, const T*, int, int, T*);             \
   template int extract_r<T>(cudaStream_t, const T*, int, int, int, T*);                 \
   template int extract_rt<T>(cudaStream_t, const T*, int, int, int, double*);           \
+  template int extract_r_f64<T>(cudaStream_t, const T*, int, int, int, double*);        \
   template int frobenius_norm<T>(cudaStream_t, const T*, long long, double*);
 TT_EW_INST(double)
 TT_EW_INST(float)

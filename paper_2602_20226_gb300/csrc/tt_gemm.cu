@@ -7,6 +7,8 @@
 // This is the GEMM of the plain FP64 form (DFMA-bound on GB300: ~1.2 TFLOP/s peak)
 // and of the FP64 environment sweeps.  64 x 64 x 16 tiles, 256 threads, 4 x 4
 // outputs per thread, tiles staged in shared memory.
+#include <type_traits>
+
 #include "tt_gemm.cuh"
 
 namespace tt {
@@ -22,16 +24,20 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
                                                        int64_t sbk, int64_t sbn, double beta,
                                                        TC* __restrict__ C, int64_t scm,
                                                        int64_t scn) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  // FP32 operands and output accumulate in FP32 (mixed form), anything else in FP64
+  using Acc = std::conditional_t<std::is_same<TA, float>::value && std::is_same<TB, float>::value &&
+                                     std::is_same<TC, float>::value,
+                                 float, double>;
+  __shared__ Acc As[BK][BM + 1];
+  __shared__ Acc Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  double acc[4][4];
+  Acc acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
 
   const bool a_m_fast = (sam == 1);
   const bool b_n_fast = (sbn == 1);
@@ -49,8 +55,8 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
         mm = e / BK;
       }
       const int gm = m0 + mm, gk = k0 + kk;
-      double v = 0.0;
-      if (gm < M && gk < K) v = (double)A[(int64_t)gm * sam + (int64_t)gk * sak];
+      Acc v = Acc(0);
+      if (gm < M && gk < K) v = (Acc)A[(int64_t)gm * sam + (int64_t)gk * sak];
       As[kk][mm] = v;
     }
 #pragma unroll
@@ -65,14 +71,14 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
         nn = e / BK;
       }
       const int gn = n0 + nn, gk = k0 + kk;
-      double v = 0.0;
-      if (gn < N && gk < K) v = (double)B[(int64_t)gk * sbk + (int64_t)gn * sbn];
+      Acc v = Acc(0);
+      if (gn < N && gk < K) v = (Acc)B[(int64_t)gk * sbk + (int64_t)gn * sbn];
       Bs[kk][nn] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      Acc a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
       const int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       TC* p = C + (int64_t)gm * scm + (int64_t)gn * scn;
-      double v = alpha * acc[i][j];
+      double v = alpha * (double)acc[i][j];
       if (beta != 0.0) v += beta * (double)(*p);
       *p = (TC)v;
     }
@@ -122,14 +128,14 @@ int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t
     const int64_t total = (int64_t)M * N;
     const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
     scale_kernel<TC><<<blocks, 256, 0, s>>>(M, N, beta, C, scm, scn);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
     return TT_OK;
   }
   dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM));
   if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm: M too large");
   gemm_simt_kernel<TA, TB, TC>
       <<<grid, NT, 0, s>>>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
@@ -146,5 +152,23 @@ TT_GEMM_INST(float, double, float)
 TT_GEMM_INST(float, float, double)
 TT_GEMM_INST(float, float, float)
 #undef TT_GEMM_INST
+
+template <>
+int gemm_fast<double>(cudaStream_t s, int M, int N, int K, double alpha, const double* A, int64_t sam,
+                      int64_t sak, const double* B, int64_t sbk, int64_t sbn, double beta, double* C,
+                      int64_t scm, int64_t scn, unsigned* status) {
+  (void)status;
+  return gemm<double, double, double>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+}
+
+template <>
+int gemm_fast<float>(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,
+                     int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
+                     int64_t scm, int64_t scn, unsigned* status) {
+  // tiny products stay on the SIMT path (a 128-row tensor-core tile would be mostly padding)
+  if ((int64_t)M * N * K < (1 << 16) || K < 8)
+    return gemm<float, float, float>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+  return gemm_tf32x3(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, status);
+}
 
 }  // namespace tt

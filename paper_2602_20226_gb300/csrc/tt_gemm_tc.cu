@@ -1,0 +1,328 @@
+// Tensor-core GEMM for the mixed form:  C = alpha * A B + beta * C  with FP32 operands,
+// computed on the 5th-generation tensor cores (tcgen05, kind::tf32) with a 3-term
+// split so the result keeps ~FP32 accuracy:
+//     x = x_hi + x_lo,  x_hi = rn_tf32(x),  x_lo = x - x_hi (exact in FP32)
+//     A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi           (the lo*lo term is < 2^-23)
+// (split-precision products: Ootomo & Yokota 2022; Henry, Tang, Heinecke 2019).
+//
+// One CTA (128 threads = 4 warps) owns a 128 x BN output tile.  The accumulator lives
+// in tensor memory (BN FP32 columns x 128 lanes).  Per 32-wide K block, all threads
+// load the A and B tiles from global memory, split them and store hi and lo parts in
+// shared memory in the no-swizzle K-major canonical layout (8-row x 16-byte core
+// matrices); then one thread issues 3 x 4 tcgen05.mma (K = 8 each) and commits them
+// to an mbarrier.  Two shared-memory stages let the loads of block k+1 overlap the
+// MMAs of block k.  Every mbarrier wait is bounded: on expiry the kernel raises
+// ST_TIMEOUT, drains (bounded), frees its tensor memory and skips the epilogue.
+#include <cstdint>
+
+#include "tt_gemm.cuh"
+
+namespace tt {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BK = 32, TC_THREADS = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (between core matrices along K), stride-dimension byte offset (between
+// 8-row groups), descriptor version 1 (bit 46), no swizzle, base offset 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = bn
+__host__ __device__ constexpr uint32_t idesc_tf32(int bn) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: ~ a second at most
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < (1ll << 22); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  hi = __uint_as_float(u);
+  lo = x - hi;
+}
+
+// byte offset of element (row, k) of a rows x 32 K-major no-swizzle tile
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+struct TcArgs {
+  int M, N, K;
+  float alpha, beta;
+  const float* A;
+  int64_t sam, sak;
+  const float* B;
+  int64_t sbk, sbn;
+  float* C;
+  int64_t scm, scn;
+  unsigned* status;
+};
+
+// Load a rows x 32 tile of an operand whose element (row, k) sits at P[row*srow + k*sk],
+// split it and store hi / lo in the canonical layout.  Rows beyond nrows and k beyond K
+// are zero.
+template <int ROWS>
+__device__ __forceinline__ void load_split(const float* __restrict__ P, int64_t srow, int64_t sk,
+                                           int row0, int nrows, int k0, int K, uint8_t* hi,
+                                           uint8_t* lo) {
+  const int tid = threadIdx.x;
+  constexpr int PER = ROWS * TC_BK / TC_THREADS;
+  if (sk == 1 || srow != 1) {  // k fastest across threads
+#pragma unroll 4
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * TC_THREADS;
+      const int k = e & 31, r = e >> 5;
+      const int gr = row0 + r, gk = k0 + k;
+      const float v = (gr < nrows && gk < K) ? __ldg(P + (int64_t)gr * srow + (int64_t)gk * sk) : 0.0f;
+      float h, l;
+      split_tf32(v, h, l);
+      const uint32_t o = tile_off(r, k);
+      *reinterpret_cast<float*>(hi + o) = h;
+      *reinterpret_cast<float*>(lo + o) = l;
+    }
+  } else {  // rows fastest across threads
+#pragma unroll 4
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * TC_THREADS;
+      const int r = e % ROWS, k = e / ROWS;
+      const int gr = row0 + r, gk = k0 + k;
+      const float v = (gr < nrows && gk < K) ? __ldg(P + (int64_t)gr * srow + (int64_t)gk * sk) : 0.0f;
+      float h, l;
+      split_tf32(v, h, l);
+      const uint32_t o = tile_off(r, k);
+      *reinterpret_cast<float*>(hi + o) = h;
+      *reinterpret_cast<float*>(lo + o) = l;
+    }
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(TcArgs g) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int A_BYTES = TC_BM * TC_BK * 4, B_BYTES = BN * TC_BK * 4;
+  constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr uint32_t IDESC = idesc_tf32(BN);
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  uint32_t phase0 = 0, phase1 = 0;
+  bool pend0 = false, pend1 = false;
+  bool ok = true;
+  const int nkb = (g.K + TC_BK - 1) / TC_BK;
+  for (int kb = 0; kb < nkb && ok; ++kb) {
+    const int s = kb & 1;
+    // the stage is free once the MMAs that read it (two blocks ago) have completed
+    if (s == 0 && pend0) {
+      ok = mbar_wait(&mbar[0], phase0);
+      phase0 ^= 1;
+      pend0 = false;
+    } else if (s == 1 && pend1) {
+      ok = mbar_wait(&mbar[1], phase1);
+      phase1 ^= 1;
+      pend1 = false;
+    }
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    uint8_t* st = smem + s * STAGE;
+    uint8_t* a_hi = st;
+    uint8_t* a_lo = st + A_BYTES;
+    uint8_t* b_hi = st + 2 * A_BYTES;
+    uint8_t* b_lo = st + 2 * A_BYTES + B_BYTES;
+    const int k0 = kb * TC_BK;
+    load_split<TC_BM>(g.A, g.sam, g.sak, m0, g.M, k0, g.K, a_hi, a_lo);
+    load_split<BN>(g.B, g.sbn, g.sbk, n0, g.N, k0, g.K, b_hi, b_lo);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+        const uint32_t off = kk * 256;  // two core matrices along K per MMA
+        const uint64_t dah = smem_desc(smem_u32(a_hi) + off, 128, 1024);
+        const uint64_t dal = smem_desc(smem_u32(a_lo) + off, 128, 1024);
+        const uint64_t dbh = smem_desc(smem_u32(b_hi) + off, 128, 1024);
+        const uint64_t dbl = smem_desc(smem_u32(b_lo) + off, 128, 1024);
+        mma_tf32(tmem, dah, dbh, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, dah, dbl, IDESC, 1u);
+        mma_tf32(tmem, dal, dbh, IDESC, 1u);
+      }
+      mma_commit(&mbar[s]);
+    }
+    if (s == 0) pend0 = true; else pend1 = true;
+  }
+  // drain: wait for every outstanding commit (bounded)
+  bool drained = true;
+  if (pend0) drained = mbar_wait(&mbar[0], phase0) && drained;
+  if (pend1) drained = mbar_wait(&mbar[1], phase1) && drained;
+  ok = __syncthreads_and(ok && drained);
+  tc_fence_after();
+
+  if (ok && nkb > 0) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(lane_base + (uint32_t)c0, r);
+      if (row < g.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < g.N) {
+            float* p = g.C + (int64_t)row * g.scm + (int64_t)col * g.scn;
+            float v = g.alpha * __uint_as_float(r[j]);
+            if (g.beta != 0.0f) v += g.beta * (*p);
+            *p = v;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                 : "memory");
+  }
+  if (!ok && tid == 0 && g.status) atomicOr(g.status, (unsigned)ST_TIMEOUT);
+}
+
+template <int BN>
+constexpr size_t tc_smem_bytes() {
+  return 2 * (2 * TC_BM * TC_BK * 4 + 2 * BN * TC_BK * 4);
+}
+
+template <int BN>
+int launch_tc(cudaStream_t s, const TcArgs& a) {
+  static int configured = -1;
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (configured != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(gemm_tf32x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes<BN>()));
+    configured = dev;
+  }
+  dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, TC_BM));
+  if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm_tf32x3: M too large");
+  gemm_tf32x3_kernel<BN><<<grid, TC_THREADS, tc_smem_bytes<BN>(), s>>>(a);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+}  // namespace
+
+int gemm_tf32x3(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,
+                int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
+                int64_t scm, int64_t scn, unsigned* status) {
+  if (M <= 0 || N <= 0) return TT_OK;
+  if (K <= 0) return gemm<float, float, float>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+  // a tile is 128 rows of M: if M is short and N long, compute C^T = B^T A^T instead
+  if (M < 96 && N > M) {
+    std::swap(M, N);
+    std::swap(A, B);
+    const int64_t t_sam = sbn, t_sak = sbk, t_sbk = sak, t_sbn = sam;
+    sam = t_sam;
+    sak = t_sak;
+    sbk = t_sbk;
+    sbn = t_sbn;
+    std::swap(scm, scn);
+  }
+  TcArgs a{M, N, K, (float)alpha, (float)beta, A, sam, sak, B, sbk, sbn, C, scm, scn, status};
+  if (N <= 64) return launch_tc<64>(s, a);
+  return launch_tc<128>(s, a);
+}
+
+}  // namespace tt

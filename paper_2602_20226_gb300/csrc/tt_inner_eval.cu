@@ -149,7 +149,7 @@ int inner_impl(const tt_train* x, const tt_train* y, double* out, void* ws, size
   double* E2 = E + env;
   double* Tb = E2 + env;
   set_scalar_kernel<<<1, 1, 0, s>>>(E, 1.0);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   for (int k = 0; k < L; ++k) {
     const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
     const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
@@ -192,7 +192,7 @@ int inner_backward_impl(const tt_train* x, const tt_train* y, double dout, tt_tr
   double* T3 = T2 + tb;
   // left environments E^L_0..E^L_{L-1}
   set_scalar_kernel<<<1, 1, 0, s>>>(EL, 1.0);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   for (int k = 0; k < L - 1; ++k) {
     const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
     const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
@@ -204,7 +204,7 @@ int inner_backward_impl(const tt_train* x, const tt_train* y, double dout, tt_tr
                                      EL + eoff[k + 1], ry1, 1)));
   }
   set_scalar_kernel<<<1, 1, 0, s>>>(ER, 1.0);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   for (int k = L - 1; k >= 0; --k) {
     const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
     const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
@@ -268,7 +268,7 @@ int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values,
   if (blocks > 0x7fffffffLL) return fail(TT_ERR_UNSUPPORTED, "tt_eval: too many samples");
   eval_kernel<T, 8><<<(unsigned)blocks, S, smem_for(S), s>>>(P, digits, n, static_cast<T*>(values),
                                                                status_dev);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
@@ -314,16 +314,16 @@ int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, cons
     double* sA = sA0;
     double* sB = sB0;
     fill_ones_kernel<<<(unsigned)ceil_div(cn, TPB), TPB, 0, s>>>(pre, cn);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
     for (int k = 0; k < L - 1; ++k) {
       const int r0 = (int)x->ranks[k], r1 = (int)x->ranks[k + 1];
       eval_step_kernel<T><<<(unsigned)ceil_div(cn * r1, TPB), TPB, 0, s>>>(
           static_cast<const T*>(x->cores[k]), r0, x->d[k], r1, dg, L, k, cn, pre + poff[k],
           pre + poff[k + 1], false);
-      TT_CUDA_CHECK(cudaGetLastError());
+      TT_LAUNCH_CHECK();
     }
     fill_ones_kernel<<<(unsigned)ceil_div(cn, TPB), TPB, 0, s>>>(sA, cn);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
     for (int k = L - 1; k >= 0; --k) {
       const int r0 = (int)x->ranks[k], r1 = (int)x->ranks[k + 1], d = x->d[k];
       if (dx->cores[k]) {
@@ -331,14 +331,14 @@ int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, cons
         TT_CUDA_CHECK(cudaMemsetAsync(acc, 0, g * sizeof(double), s));
         dim3 grid((unsigned)std::min<int64_t>(std::max<int64_t>(1, cn / 256), 256), (unsigned)r0);
         eval_bwd_site_kernel<T><<<grid, 128, 0, s>>>(pre + poff[k], sA, w, dg, L, k, cn, r0, d, r1, acc);
-        TT_CUDA_CHECK(cudaGetLastError());
+        TT_LAUNCH_CHECK();
         add_into_kernel<T><<<(unsigned)ceil_div(g, TPB), TPB, 0, s>>>(acc, g, static_cast<T*>(dx->cores[k]));
-        TT_CUDA_CHECK(cudaGetLastError());
+        TT_LAUNCH_CHECK();
       }
       if (k > 0) {
         eval_step_kernel<T><<<(unsigned)ceil_div(cn * r0, TPB), TPB, 0, s>>>(
             static_cast<const T*>(x->cores[k]), r0, d, r1, dg, L, k, cn, sA, sB, true);
-        TT_CUDA_CHECK(cudaGetLastError());
+        TT_LAUNCH_CHECK();
         std::swap(sA, sB);
       }
     }

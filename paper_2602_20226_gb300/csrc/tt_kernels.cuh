@@ -85,6 +85,8 @@ int extract_r(cudaStream_t s, const T* A, int lda, int p, int n, T* R);
 template <typename T>
 int extract_rt(cudaStream_t s, const T* A, int lda, int p, int n, double* X);
 template <typename T>
+int extract_r_f64(cudaStream_t s, const T* A, int lda, int p, int n, double* X);
+template <typename T>
 int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out);
 
 }  // namespace tt

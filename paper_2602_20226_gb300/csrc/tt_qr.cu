@@ -8,7 +8,9 @@
 // followed by a cross-warp sum in shared memory.
 //
 // Trailing update A <- (I - V T^T V^T) A and thin-Q formation
-// Q = H_1 ... H_p [I; 0] use three GEMMs per panel (W = V^T A, W <- T^(T) W, A -= V W).
+// Q = H_1 ... H_p [I; 0] take two launches per panel: W2 = op(T) V^T A (one CTA per
+// column, a reduction over the rows) and the rank-nb update A -= V W2 (the GEMM of
+// the form: FP64 SIMT, or tensor cores for FP32).
 #include "tt_qr.cuh"
 
 namespace tt {
@@ -118,6 +120,49 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
   }
 }
 
+// W2[:, c] = op(T) (V^T A[:, c]) for one column c per CTA, jb <= 32:
+// the small-M half of applying the block reflector I - V T V^T (op(T) = T^T when
+// building R, T when building Q).  V (mr x jb) and A (mr x nc) are column-major.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) reflector_w_kernel(const T* __restrict__ V, int ldv,
+                                                         const T* __restrict__ A, int lda, int mr,
+                                                         int jb, const T* __restrict__ Tm, int ldt,
+                                                         bool transpose_t, T* __restrict__ W2) {
+  constexpr int NW = NT / 32;
+  __shared__ T red[NW][33];
+  __shared__ T w[32];
+  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* a = A + (int64_t)c * lda;
+  T acc[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) acc[t] = T(0);
+  for (int i = tid; i < mr; i += NT) {
+    const T ai = a[i];
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      if (t < jb) acc[t] += V[i + (int64_t)t * ldv] * ai;
+  }
+  warp_reduce_scatter32(acc, lane);
+  red[warp][lane] = acc[0];
+  __syncthreads();
+  if (tid < 32) {
+    T v = T(0);
+#pragma unroll
+    for (int q = 0; q < NW; ++q) v += red[q][tid];
+    w[tid] = v;
+  }
+  __syncthreads();
+  if (tid < jb) {
+    T v = T(0);
+    if (transpose_t) {  // (T^T w)_t = sum_{q <= t} T[q, t] w_q
+      for (int q = 0; q <= tid; ++q) v += Tm[q + (int64_t)tid * ldt] * w[q];
+    } else {  // (T w)_t = sum_{q >= t} T[t, q] w_q
+      for (int q = tid; q < jb; ++q) v += Tm[tid + (int64_t)q * ldt] * w[q];
+    }
+    W2[tid + (int64_t)c * jb] = v;
+  }
+}
+
 template <typename T>
 __global__ void init_thin_q_kernel(T* Q, int m, int p, int ldq) {
   const int64_t total = (int64_t)m * p;
@@ -139,18 +184,17 @@ int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
     const int jb = std::min(nb, p - j0);
     T* Tm = w.tmat + (int64_t)panel * nb * nb;
     qr_panel_kernel<T, 512><<<1, 512, 0, s>>>(A, lda, m, j0, jb, w.tau, Tm, nb, w.vbuf, w.ldv);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
     const int nt = n - (j0 + jb);
     if (nt <= 0) continue;
     const int mr = m - j0;
     const T* V = w.vbuf + j0 + (int64_t)j0 * w.ldv;
     T* At = A + j0 + (int64_t)(j0 + jb) * lda;
-    // W = V^T At   (jb x nt, column-major ld jb)
-    TT_TRY(gemm<T, T, T>(s, jb, nt, mr, 1.0, V, w.ldv, 1, At, 1, lda, 0.0, w.w1, 1, jb));
-    // W2 = T^T W
-    TT_TRY(gemm<T, T, T>(s, jb, nt, jb, 1.0, Tm, nb, 1, w.w1, 1, jb, 0.0, w.w2, 1, jb));
+    // W2 = T^T (V^T At)   (jb x nt, column-major ld jb)
+    reflector_w_kernel<T, 256><<<nt, 256, 0, s>>>(V, w.ldv, At, lda, mr, jb, Tm, nb, true, w.w2);
+    TT_LAUNCH_CHECK();
     // At -= V W2
-    TT_TRY(gemm<T, T, T>(s, mr, nt, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, At, 1, lda));
+    TT_TRY(gemm_fast<T>(s, mr, nt, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, At, 1, lda, nullptr));
   }
   w.m = m;
   w.n = n;
@@ -165,7 +209,7 @@ int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq) {
     const int64_t total = (int64_t)m * p;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 8192));
     init_thin_q_kernel<T><<<blocks, 256, 0, s>>>(Q, m, p, ldq);
-    TT_CUDA_CHECK(cudaGetLastError());
+    TT_LAUNCH_CHECK();
   }
   for (int panel = w.npanels - 1; panel >= 0; --panel) {
     const int j0 = panel * nb;
@@ -174,10 +218,10 @@ int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq) {
     const T* V = w.vbuf + j0 + (int64_t)j0 * w.ldv;
     const T* Tm = w.tmat + (int64_t)panel * nb * nb;
     T* Qs = Q + j0 + (int64_t)j0 * ldq;
-    // W = V^T Qs ; W2 = T W ; Qs -= V W2
-    TT_TRY(gemm<T, T, T>(s, jb, nc, mr, 1.0, V, w.ldv, 1, Qs, 1, ldq, 0.0, w.w1, 1, jb));
-    TT_TRY(gemm<T, T, T>(s, jb, nc, jb, 1.0, Tm, 1, nb, w.w1, 1, jb, 0.0, w.w2, 1, jb));
-    TT_TRY(gemm<T, T, T>(s, mr, nc, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, Qs, 1, ldq));
+    // W2 = T (V^T Qs) ; Qs -= V W2
+    reflector_w_kernel<T, 256><<<nc, 256, 0, s>>>(V, w.ldv, Qs, ldq, mr, jb, Tm, nb, false, w.w2);
+    TT_LAUNCH_CHECK();
+    TT_TRY(gemm_fast<T>(s, mr, nc, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, Qs, 1, ldq, nullptr));
   }
   return TT_OK;
 }

@@ -4,7 +4,10 @@
 // The output cores double as the working cores: x is copied into out (whose slots
 // hold x's ranks), then every step rewrites slots in place.  Ranks never grow, so the
 // slots always suffice.  All scratch is carved from the caller's workspace.
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "tt_kernels.cuh"
@@ -67,7 +70,6 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   B.vsel = c.take<T>((size_t)D.r_max * D.r_max);
   B.F = c.take<T>((size_t)D.r_max * D.r_max);
   B.sv.X = c.take<double>((size_t)D.r_max * D.r_max);
-  B.sv.V = c.take<double>((size_t)D.r_max * D.r_max);
   B.sv.sigma = c.take<double>(D.r_max);
   B.sv.perm = c.take<int>(D.r_max);
   B.sv.rank = c.take<int>(1);
@@ -88,6 +90,80 @@ template <typename T>
 double jacobi_tol(int nrow) {
   // columns are treated as orthogonal once |x_a . x_b| <= tol ||x_a|| ||x_b||
   return std::sqrt((double)std::max(nrow, 1)) * 2.220446049250313e-16;
+}
+
+// Opt-in phase timer (environment variable TT_TRACE=1): synchronises the stream at
+// phase boundaries and prints the wall time per phase to stderr at the end.
+struct PhaseTimer {
+  bool on = std::getenv("TT_TRACE") != nullptr;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t0;
+  double acc[8] = {0};
+  const char* names[8] = {"rl_qr", "rl_formq", "rl_gemm", "lr_qr", "lr_formq", "lr_jacobi",
+                          "lr_truncate", "lr_gemm"};
+  explicit PhaseTimer(cudaStream_t st) : s(st) { mark(-1); }
+  void mark(int phase) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    auto t = std::chrono::steady_clock::now();
+    if (phase >= 0) acc[phase] += std::chrono::duration<double, std::milli>(t - t0).count();
+    t0 = t;
+  }
+  ~PhaseTimer() {
+    if (!on) return;
+    std::fprintf(stderr, "[tt_round trace]");
+    for (int i = 0; i < 8; ++i) std::fprintf(stderr, " %s=%.2fms", names[i], acc[i]);
+    std::fprintf(stderr, "\n");
+  }
+};
+
+// Event timing of the round's phases on the launching stream (tt_profile_enable):
+// an event pair brackets every Jacobi launch, every QR (+ thin Q) and every GEMM
+// group; the pairs are read back at the per-bond synchronisation that the sweep
+// needs anyway, so profiling adds no extra stream synchronisation.
+struct EventProfiler {
+  bool on = profile_enabled();
+  cudaStream_t s;
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::pair<int, double>> open;  // (class, nominal flops) per event pair
+  explicit EventProfiler(cudaStream_t st) : s(st) {}
+  ~EventProfiler() {
+    flush();
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  int begin() {
+    if (!on) return -1;
+    const size_t i = open.size();
+    while (ev.size() < 2 * (i + 1)) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+    cudaEventRecord(ev[2 * i], s);
+    open.push_back({-1, 0.0});
+    return (int)i;
+  }
+  void end(int i, int cls, double flops) {
+    if (!on || i < 0) return;
+    cudaEventRecord(ev[2 * i + 1], s);
+    open[i] = {cls, flops};
+  }
+  // call after the stream has been synchronised
+  void flush() {
+    if (!on) return;
+    for (size_t i = 0; i < open.size(); ++i) {
+      if (open[i].first < 0) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) == cudaSuccess)
+        profile_add(open[i].first, ms, open[i].second);
+    }
+    open.clear();
+  }
+};
+
+double qr_nominal(int m, int n) {
+  const double a = std::max(m, n), b = std::min(m, n);
+  return 4.0 * a * b * b - 4.0 * b * b * b / 3.0;
 }
 
 int read_back(cudaStream_t s, const void* dev, void* host, size_t bytes) {
@@ -127,6 +203,8 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
     TT_CUDA_CHECK(cudaMemcpyAsync(slot[k], x->cores[k], n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   }
   TT_CUDA_CHECK(cudaMemsetAsync(B.sv.status, 0, sizeof(unsigned), s));
+  PhaseTimer tm(s);
+  EventProfiler prof(s);
 
   // ---- 1. right-to-left: LQ of C_k (r_{k-1} x d r_k) as the QR of its transpose
   for (int k = L - 1; k >= 1; --k) {
@@ -134,14 +212,22 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
     const int m = dk * r1, n = r0, p = std::min(m, n);
     TT_CUDA_CHECK(cudaMemcpyAsync(B.A, slot[k], (size_t)m * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     B.qr.ldv = m;
+    int pe = prof.begin();
     TT_TRY(householder_qr<T>(s, B.A, m, n, m, B.qr));
+    tm.mark(0);
     TT_TRY(form_thin_q<T>(s, B.qr, slot[k], m));  // Q^T row-major = new core [p][d][r1]
+    prof.end(pe, PROF_QR, qr_nominal(m, n));
+    tm.mark(1);
     TT_TRY(extract_r<T>(s, B.A, m, p, n, B.Rbuf));
     const int rows = (int)cur[k - 1] * d[k - 1];
     // C_{k-1} <- C_{k-1} R^T
-    TT_TRY((gemm<T, T, T>(s, rows, p, n, 1.0, slot[k - 1], n, 1, B.Rbuf, p, 1, 0.0, B.tmp, p, 1)));
+    pe = prof.begin();
+    TT_TRY((gemm_fast<T>(s, rows, p, n, 1.0, slot[k - 1], n, 1, B.Rbuf, p, 1, 0.0, B.tmp, p, 1,
+                         B.sv.status)));
+    prof.end(pe, PROF_GEMM, 2.0 * rows * p * n);
     TT_CUDA_CHECK(cudaMemcpyAsync(slot[k - 1], B.tmp, (size_t)rows * p * sizeof(T),
                                   cudaMemcpyDeviceToDevice, s));
+    tm.mark(2);
     cur[k] = p;
   }
   TT_TRY(frobenius_norm<T>(s, slot[0], cur[0] * d[0] * cur[1], B.sv.norm));
@@ -153,39 +239,79 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
     for (int k = 0; k < L - 1; ++k) {
       const int r0 = (int)cur[k], r1 = (int)cur[k + 1];
       const int m = r0 * d[k], n = r1, p = std::min(m, n);
-      TT_TRY(transpose_rm_to_cm<T>(s, slot[k], m, n, B.A));
-      B.qr.ldv = m;
-      TT_TRY(householder_qr<T>(s, B.A, m, n, m, B.qr));
-      TT_TRY(form_thin_q<T>(s, B.qr, B.Q, m));
-      B.sv.ldx = n;
-      B.sv.ldv = p;
-      TT_TRY(extract_rt<T>(s, B.A, m, p, n, B.sv.X));
-      TT_TRY(jacobi_svd(s, B.sv, n, p, jacobi_tol<T>(n), 30));
-      TT_TRY(svd_truncate(s, B.sv, n, p, delta_scale, max_rank));
+      const bool tall = m >= n;
+      int pe = prof.begin();
+      if (tall) {
+        // QR of C_k (m x n): C_k = Q R with R square (n x n); SVD of R
+        TT_TRY(transpose_rm_to_cm<T>(s, slot[k], m, n, B.A));
+        B.qr.ldv = m;
+        TT_TRY(householder_qr<T>(s, B.A, m, n, m, B.qr));
+        tm.mark(3);
+        TT_TRY(form_thin_q<T>(s, B.qr, B.Q, m));
+        tm.mark(4);
+        // R (n x n) twice: in T for the right factor, in FP64 for the Jacobi SVD
+        TT_TRY(extract_r<T>(s, B.A, m, p, n, B.Rbuf));
+        B.sv.ldx = n;
+        TT_TRY(extract_r_f64<T>(s, B.A, m, p, n, B.sv.X));
+      } else {
+        // wide core (m < n): LQ of C_k, i.e. the QR of C_k^T (n x m), whose column-major
+        // form is C_k's own row-major memory: C_k = Rt^T Qt^T.  The left singular vectors
+        // of C_k are those of the square lower-triangular Rt^T (m x m).
+        TT_CUDA_CHECK(cudaMemcpyAsync(B.A, slot[k], (size_t)m * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        B.qr.ldv = n;
+        TT_TRY(householder_qr<T>(s, B.A, n, m, n, B.qr));
+        tm.mark(3);
+        B.sv.ldx = m;
+        TT_TRY(extract_rt<T>(s, B.A, n, m, m, B.sv.X));
+        tm.mark(4);
+      }
+      prof.end(pe, PROF_QR, qr_nominal(m, n));
+      pe = prof.begin();
+      // one-sided Jacobi on the columns of the square factor X (p x p)
+      TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30));
+      prof.end(pe, PROF_JACOBI, 12.0 * p * (double)p * p);
+      tm.mark(5);
+      TT_TRY(svd_truncate(s, B.sv, p, p, delta_scale, max_rank));
       int rk[2] = {0, 0};
       TT_TRY(read_back(s, B.sv.rank, &rk[0], sizeof(int)));
       TT_TRY(read_back(s, B.sv.sweeps, &rk[1], sizeof(int)));
       total_sweeps += rk[1];
+      prof.flush();
+      tm.mark(6);
       const int rn = rk[0];
       if (rn < 1 || rn > p) return fail(TT_ERR_NUMERIC, "tt_round: invalid truncation rank");
-      TT_TRY(svd_gather<T>(s, B.sv, n, p, rn, B.vsel, B.F));
-      // C_k <- Q V[:, perm[:r']]   (m x r', row-major)
-      TT_TRY((gemm<T, T, T>(s, m, rn, p, 1.0, B.Q, 1, m, B.vsel, 1, p, 0.0, slot[k], rn, 1)));
-      // C_{k+1} <- W[:, perm[:r']]^T C_{k+1}
+      // U_r (p x r') = X[:, perm[:r']] / sigma
+      pe = prof.begin();
+      TT_TRY(svd_left_vectors<T>(s, B.sv, p, rn, B.vsel));
+      if (tall) {
+        // C_k <- Q U_r (m x r', row-major);  F = U_r^T R (r' x n, row-major)
+        TT_TRY((gemm_fast<T>(s, m, rn, p, 1.0, B.Q, 1, m, B.vsel, 1, p, 0.0, slot[k], rn, 1, B.sv.status)));
+        TT_TRY((gemm_fast<T>(s, rn, n, p, 1.0, B.vsel, p, 1, B.Rbuf, 1, p, 0.0, B.F, n, 1, B.sv.status)));
+      } else {
+        // F = U_r^T C_k (r' x n) from the original core, then C_k <- U_r (m x r', row-major)
+        TT_TRY((gemm_fast<T>(s, rn, n, m, 1.0, B.vsel, m, 1, slot[k], n, 1, 0.0, B.F, n, 1, B.sv.status)));
+        TT_TRY(transpose_rm_to_cm<T>(s, B.vsel, rn, m, slot[k]));
+      }
       const int cols = d[k + 1] * (int)cur[k + 2];
-      TT_TRY((gemm<T, T, T>(s, rn, cols, n, 1.0, B.F, n, 1, slot[k + 1], cols, 1, 0.0, B.tmp, cols, 1)));
+      TT_TRY((gemm_fast<T>(s, rn, cols, n, 1.0, B.F, n, 1, slot[k + 1], cols, 1, 0.0, B.tmp, cols, 1,
+                           B.sv.status)));
       TT_CUDA_CHECK(cudaMemcpyAsync(slot[k + 1], B.tmp, (size_t)rn * cols * sizeof(T),
                                     cudaMemcpyDeviceToDevice, s));
+      prof.end(pe, PROF_GEMM,
+               (tall ? 2.0 * m * rn * p + 2.0 * rn * n * p : 2.0 * rn * n * m) + 2.0 * rn * cols * n);
+      tm.mark(7);
       cur[k + 1] = rn;
     }
   }
   double nrm = 0.0;
   unsigned st = 0;
   TT_TRY(read_back(s, B.sv.norm, &nrm, sizeof(double)));
+  prof.flush();
   TT_TRY(read_back(s, B.sv.status, &st, sizeof(unsigned)));
   for (int k = 0; k <= L; ++k) out->ranks[k] = cur[k];
   if (norm_out) *norm_out = nrm;
   if (stats) stats->jacobi_sweeps = total_sweeps;
+  if (tm.on) std::fprintf(stderr, "[tt_round trace] jacobi sweeps total=%d\n", total_sweeps);
   if (!std::isfinite(nrm) || (st & ST_NONFINITE)) return fail(TT_ERR_NUMERIC, "tt_round: non-finite values");
   if (st & ST_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_round: device wait expired");
   if (st & ST_NONCONVERGED) return fail(TT_ERR_NUMERIC, "tt_round: Jacobi SVD hit its sweep cap");

@@ -1,14 +1,16 @@
 // FP64 bond SVD by one-sided Jacobi (Hestenes), truncation decision, gather.
 //
 // The rounding sweep needs the SVD of R (p x n, from the QR of a core).  We run
-// one-sided Jacobi on the columns of X = R^T (n x p): plane rotations J make the
-// columns of W = X V mutually orthogonal, so R = V W^T = V diag(sigma) (W/sigma)^T.
-// Then U = V is exactly orthogonal (a product of rotations), sigma_j = ||W_j||, and
-// the truncated factors are
-//     C_k     <- Q V[:, perm[:r']]          (orthonormal columns)
-//     C_{k+1} <- W[:, perm[:r']]^T C_{k+1}  (sigma-scaled right factor)
-// The dropped part has Frobenius norm sqrt(sum_{dropped} ||W_j||^2) exactly, so the
-// rounding bound holds even before the last sweep.
+// one-sided Jacobi on the columns of X = R: plane rotations J make the columns of
+// W = R J mutually orthogonal, so R = W J^T = U diag(sigma) V^T with sigma_j = ||W_j||
+// and U = W diag(1/sigma).  The rotations are NOT accumulated: the truncated factors
+// are formed from U alone,
+//     C_k     <- Q U[:, perm[:r']]                  (orthonormal columns)
+//     C_{k+1} <- (U[:, perm[:r']]^T R) C_{k+1}      (= (S V^T)[:r'] C_{k+1})
+// so the kept part is an orthogonal projection of R whatever rounding the rotation
+// sequence accumulated.  (Accumulating J over the ~p rotations per column per sweep
+// leaves ||J^T J - I|| ~ 1e-12 at p = 320, which showed up as a 1e-12 error of
+// the rounded train; U's orthogonality is set directly by the stopping test.)
 //
 // Parallel ordering: round-robin tournament over the p columns; every round's p/2
 // rotations are independent.  One warp per column pair, CTAs synchronised between
@@ -32,8 +34,7 @@ __device__ __forceinline__ bool sweep_barrier(unsigned* bar, unsigned* status) {
 
 template <int NT>
 __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int ncol, int ldx,
-                                                    double* V, int ldv, double tol,
-                                                    int max_sweeps, unsigned* bar,
+                                                    double tol, int max_sweeps, unsigned* bar,
                                                     unsigned* rot, unsigned* status,
                                                     int* sweeps_out) {
   constexpr int WPB = NT / 32;
@@ -42,16 +43,6 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
   const int GW = gridDim.x * WPB;
   const int N = ncol + (ncol & 1);
   const int npairs = N / 2;
-
-  // V = I
-  {
-    const int64_t total = (int64_t)ncol * ncol;
-    for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < total; e += (int64_t)gridDim.x * NT) {
-      const int i = (int)(e % ncol), c = (int)(e / ncol);
-      __stcg(V + i + (int64_t)c * ldv, i == c ? 1.0 : 0.0);
-    }
-  }
-  if (!sweep_barrier(bar, status)) return;
 
   int sweep = 0;
   bool converged = false;
@@ -91,17 +82,11 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
                                : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t);
           const double s = c * t;
+          if (s == 0.0) continue;  // angle below resolution: nothing to rotate
           for (int i = lane; i < nrow; i += 32) {
             const double u = __ldcg(xa + i), v = __ldcg(xb + i);
             __stcg(xa + i, c * u - s * v);
             __stcg(xb + i, s * u + c * v);
-          }
-          double* va = V + (int64_t)a * ldv;
-          double* vb = V + (int64_t)b * ldv;
-          for (int i = lane; i < ncol; i += 32) {
-            const double u = __ldcg(va + i), v = __ldcg(vb + i);
-            __stcg(va + i, c * u - s * v);
-            __stcg(vb + i, s * u + c * v);
           }
           if (lane == 0) atomicAdd(rot + sweep, 1u);
         }
@@ -166,26 +151,23 @@ __global__ void __launch_bounds__(1024) svd_truncate_kernel(
     }
     for (int j = 0; j < ncol; ++j) finite = finite && isfinite(srt[j]);
     if (!finite) atomicOr(status, (unsigned)ST_NONFINITE);
+    if (r > nrow) r = nrow;  // R has rank <= its row count
     if (r < 1) r = 1;
     if (max_rank > 0 && r > max_rank) r = (int)max_rank;
     *rank_out = r;
   }
 }
 
+// U[:, t] = X[:, perm[t]] / sigma_t  (nrow x r, column-major); zero column if sigma_t = 0
 template <typename TO>
-__global__ void svd_gather_kernel(const double* X, int nrow, int ldx, const double* V, int p,
-                                  int ldv, const int* perm, int r, TO* Vsel, TO* F) {
-  const int64_t nv = (int64_t)p * r, nf = (int64_t)r * nrow;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv + nf;
+__global__ void svd_left_kernel(const double* X, int nrow, int ldx, const int* perm,
+                                const double* sig_sorted, int r, TO* U) {
+  const int64_t total = (int64_t)nrow * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < nv) {
-      const int i = (int)(e % p), t = (int)(e / p);
-      Vsel[e] = (TO)__ldcg(V + i + (int64_t)perm[t] * ldv);
-    } else {
-      const int64_t f = e - nv;
-      const int c = (int)(f % nrow), t = (int)(f / nrow);
-      F[f] = (TO)__ldcg(X + c + (int64_t)perm[t] * ldx);
-    }
+    const int i = (int)(e % nrow), t = (int)(e / nrow);
+    const double sg = sig_sorted[t];
+    U[e] = (sg > 0.0) ? (TO)(__ldcg(X + i + (int64_t)perm[t] * ldx) / sg) : TO(0);
   }
 }
 
@@ -216,9 +198,9 @@ int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int m
   TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
   const int npairs = (ncol + 1) / 2;
   if (ncol <= 48) {
-    jacobi_kernel<256><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, w.V, w.ldv, tol, max_sweeps,
-                                          w.bar, w.rot, w.status, w.sweeps);
-    TT_CUDA_CHECK(cudaGetLastError());
+    jacobi_kernel<256><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, max_sweeps, w.bar, w.rot,
+                                          w.status, w.sweeps);
+    TT_LAUNCH_CHECK();
     return TT_OK;
   }
   constexpr int NT = 64;
@@ -226,13 +208,13 @@ int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int m
   int blocks = (int)std::min<int64_t>(ceil_div(npairs, NT / 32), maxb);
   if (blocks < 1) blocks = 1;
   double* X = w.X;
-  double* V = w.V;
-  int ldx = w.ldx, ldv = w.ldv;
+  int ldx = w.ldx;
   unsigned *bar = w.bar, *rot = w.rot, *st = w.status;
   int* sw = w.sweeps;
-  void* args[] = {&X, &nrow, &ncol, &ldx, &V, &ldv, &tol, &max_sweeps, &bar, &rot, &st, &sw};
+  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &max_sweeps, &bar, &rot, &st, &sw};
   TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<NT>, dim3(blocks), dim3(NT),
                                             args, 0, s));
+  note_launch();
   return TT_OK;
 }
 
@@ -250,20 +232,20 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
   }
   svd_truncate_kernel<<<1, 1024, smem, s>>>(w.X, nrow, ncol, w.ldx, w.norm, delta_scale,
                                             (long long)max_rank, w.sigma, w.perm, w.rank, w.status);
-  TT_CUDA_CHECK(cudaGetLastError());
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
 template <typename TO>
-int svd_gather(cudaStream_t s, const SvdWork& w, int nrow, int ncol, int r, TO* Vsel, TO* F) {
-  const int64_t total = (int64_t)ncol * r + (int64_t)r * nrow;
+int svd_left_vectors(cudaStream_t s, const SvdWork& w, int nrow, int r, TO* U) {
+  const int64_t total = (int64_t)nrow * r;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 4096));
-  svd_gather_kernel<TO><<<blocks, 256, 0, s>>>(w.X, nrow, w.ldx, w.V, ncol, w.ldv, w.perm, r, Vsel, F);
-  TT_CUDA_CHECK(cudaGetLastError());
+  svd_left_kernel<TO><<<blocks, 256, 0, s>>>(w.X, nrow, w.ldx, w.perm, w.sigma, r, U);
+  TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
-template int svd_gather<double>(cudaStream_t, const SvdWork&, int, int, int, double*, double*);
-template int svd_gather<float>(cudaStream_t, const SvdWork&, int, int, int, float*, float*);
+template int svd_left_vectors<double>(cudaStream_t, const SvdWork&, int, int, double*);
+template int svd_left_vectors<float>(cudaStream_t, const SvdWork&, int, int, float*);
 
 }  // namespace tt

@@ -7,10 +7,8 @@ namespace tt {
 
 struct SvdWork {
   static constexpr int kMaxSweeps = 40;
-  double* X = nullptr;  // n x p, column-major (X = R^T), ld ldx
+  double* X = nullptr;  // p x n, column-major (X = R), ld ldx; rotated in place
   int ldx = 0;
-  double* V = nullptr;  // p x p, column-major, ld ldv
-  int ldv = 0;
   double* sigma = nullptr;  // [p] sorted descending
   int* perm = nullptr;      // [p] column of sigma_sorted[t]
   int* rank = nullptr;      // device int: truncated rank
@@ -21,15 +19,15 @@ struct SvdWork {
   double* norm = nullptr;   // device double ||x||
 };
 
-// One-sided Jacobi on the columns of X (nrow x ncol); V accumulates the rotations.
+// One-sided Jacobi on the columns of X (nrow x ncol); the rotations are not kept.
 int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps);
 
 // sigma, perm and the truncation rank with delta = delta_scale * (*norm).
 int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
                  int64_t max_rank);
 
-// Vsel (ncol x r, column-major) = V[:, perm[:r]];  F (r x nrow, row-major) = X[:, perm[:r]]^T.
+// U (nrow x r, column-major) = X[:, perm[:r]] / sigma[:r]  (left singular vectors).
 template <typename TO>
-int svd_gather(cudaStream_t s, const SvdWork& w, int nrow, int ncol, int r, TO* Vsel, TO* F);
+int svd_left_vectors(cudaStream_t s, const SvdWork& w, int nrow, int r, TO* U);
 
 }  // namespace tt

@@ -1,0 +1,126 @@
+"""GPU checks of the tensor-core (tcgen05, 3xTF32) GEMM and of the mixed form of rounding.
+
+GEMM bound: with x = x_hi + x_lo (x_hi = rn_tf32(x), |x_lo| <= 2^-12 |x|), each product
+keeps A_hi B_hi + A_hi B_lo + A_lo B_hi; the dropped A_lo B_lo and the TF32 conversion
+of the lo parts cost at most 2^-22 |a b|, and FP32 accumulation of K terms at most
+K 2^-24 sum |a b|.  So |C - AB| <= (4 + K) 2^-24 (|A| |B|) elementwise.  The tensor
+cores do not accumulate with IEEE round-to-nearest, so the relative RMS error grows
+like sqrt(K) 2^-24 times a small factor (measured 4.6e-6 at K = 640); the RMS check
+allows 4e-7 sqrt(K), far below the ~1e-4 a TF32-only product (lo terms missing) gives.
+
+Mixed rounding: FP32 cores, QR panels in FP32, GEMMs on the tensor cores, Jacobi SVD
+and truncation in FP64.  Compared with the FP64 oracle run on the same FP32 values,
+e(gpu, oracle) must stay <= 1e-6 (the accuracy target of the mixed form).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import core, structured
+from paper_2602_20226_gb300 import inputs, qtt
+
+pytestmark = pytest.mark.gpu
+
+
+def _gemm(lib, A, B, C, alpha=1.0, beta=0.0, a_cm=False, b_cm=False):
+    M, K = A.shape
+    N = B.shape[1]
+    Ad = torch.as_tensor(A.T.copy() if a_cm else A, device="cuda")
+    Bd = torch.as_tensor(B.T.copy() if b_cm else B, device="cuda")
+    Cd = torch.as_tensor(C, device="cuda")
+    sam, sak = (1, M) if a_cm else (K, 1)
+    sbk, sbn = (1, K) if b_cm else (N, 1)
+    code = lib.tt_gemm_f32(M, N, K, alpha, ctypes.c_void_p(Ad.data_ptr()), sam, sak,
+                           ctypes.c_void_p(Bd.data_ptr()), sbk, sbn, beta,
+                           ctypes.c_void_p(Cd.data_ptr()), N, 1, None)
+    assert code == 0, lib.tt_last_error()
+    torch.cuda.synchronize()
+    return Cd.cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,K,a_cm,b_cm", [
+    (128, 128, 32, False, False),
+    (300, 200, 100, True, False),
+    (64, 1000, 77, False, True),   # short M: computed as C^T = B^T A^T
+    (1000, 40, 640, True, True),
+    (7, 5, 3, False, False),       # tiny: SIMT fallback inside the dispatcher is not used here
+    (256, 320, 1280, False, False),
+])
+def test_gemm_f32_tensor_cores(cuda_lib, M, N, K, a_cm, b_cm):
+    lib = cuda_lib.load()
+    g = np.random.default_rng(M * 7 + N * 3 + K)
+    A = g.standard_normal((M, K)).astype(np.float32)
+    B = g.standard_normal((K, N)).astype(np.float32)
+    C0 = g.standard_normal((M, N)).astype(np.float32)
+    got = _gemm(lib, A, B, C0.copy(), 1.5, -0.5, a_cm, b_cm)
+    ref = 1.5 * (A.astype(np.float64) @ B.astype(np.float64)) - 0.5 * C0.astype(np.float64)
+    bound = (4 + K) * 2.0 ** -24 * (1.5 * np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
+                                     + 0.5 * np.abs(C0)) + 1e-30
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+    rel_rms = np.sqrt(np.mean(err ** 2) / np.mean(ref ** 2))
+    assert rel_rms < 4e-7 * np.sqrt(K) + 1e-7, rel_rms
+
+
+def test_gemm_f32_twice_identical(cuda_lib):
+    lib = cuda_lib.load()
+    g = np.random.default_rng(5)
+    A = g.standard_normal((500, 300)).astype(np.float32)
+    B = g.standard_normal((300, 260)).astype(np.float32)
+    a = _gemm(lib, A, B, np.zeros((500, 260), np.float32))
+    b = _gemm(lib, A, B, np.zeros((500, 260), np.float32))
+    assert np.array_equal(a, b)
+
+
+def _f32(cores):
+    return [c.astype(np.float32).astype(np.float64) for c in cores]
+
+
+def _mixed_round(tt, y32, eps):
+    Y = tt.TT.from_numpy(y32, dtype=torch.float32)
+    Z, nrm = tt.tt_round(Y, eps, prec=tt.TT_PREC_MIXED)
+    return Z.numpy(), nrm
+
+
+def test_mixed_round_c1(cuda_lib):
+    x = _f32(inputs.random_tt(1, 10, 2, 8))
+    y = _f32(core.apply_mpo(structured.laplacian_mpo(1, 10), x))
+    ref, info = core.round_tt(y, 1e-6, return_info=True)
+    got, nrm = _mixed_round(cuda_lib, y, 1e-6)
+    assert abs(nrm - info["norm"]) <= 1e-6 * info["norm"]
+    assert core.rel_err(got, ref) <= 1e-6
+    assert core.rel_err(got, y) <= 1e-6 * 1.01 + 1e-6
+
+
+def test_mixed_round_c2_shapes(cuda_lib):
+    """L = 40, r = 64, 2D Laplacian (n = 320), eps = 1e-6, FP32 cores."""
+    tt = cuda_lib
+    x = _f32(inputs.random_tt(2, 40, 2, 64))
+    W = qtt.laplacian_mpo(2, 20)
+    Y = tt.tt_apply_mpo(tt.MPO.from_numpy(W, dtype=torch.float32), tt.TT.from_numpy(x, dtype=torch.float32))
+    y = Y.numpy()
+    Z, nrm = tt.tt_round(Y, 1e-6, prec=tt.TT_PREC_MIXED)
+    ref, info = core.round_tt(y, 1e-6, return_info=True)
+    got = Z.numpy()
+    e = core.rel_err(got, ref)
+    assert e <= 1e-6, e
+    # orthogonality of the left cores, stated for the mixed form (FP32 storage)
+    worst = max(core.left_orthogonality_defect(got[k]) for k in range(0, 39, 5))
+    assert worst <= 1e-4, worst
+
+
+@pytest.mark.parametrize("case", ["modes", "wide_left", "hadamard"])
+def test_mixed_round_ragged(cuda_lib, case):
+    tt = cuda_lib
+    if case == "modes":
+        x = _f32(inputs.random_tt(3, 6, [2, 3, 5, 2, 3, 2], [1, 6, 7, 9, 5, 4, 1]))
+    elif case == "wide_left":
+        x = _f32(inputs.random_tt(8, 5, 2, [1, 40, 40, 40, 40, 1]))
+    else:
+        h = inputs.random_tt(11, 12, 2, 5)
+        x = _f32(core.hadamard(h, h))
+    ref = core.round_tt(x, 1e-6)
+    got, _ = _mixed_round(tt, x, 1e-6)
+    assert core.rel_err(got, ref) <= 1e-6
