@@ -189,6 +189,7 @@ uint64_t tt_launch_count(void);
  *   class 0  Jacobi SVD launches (12 p^3 flops each for a p x p factor)
  *   class 1  Householder QR with thin Q (4 m n^2 - 4 n^3 / 3)
  *   class 2  the GEMMs that form the new cores (2 m n k)
+ *   class 3  full-rank certificates (p^3 / 3 flops: the inverse of a p x p triangle)
  * tt_profile_read returns TT_ERR_ARG for an unknown class. */
 void tt_profile_enable(int32_t on);
 int tt_profile_read(int32_t cls, double* ms, double* nominal_flops, uint64_t* count);

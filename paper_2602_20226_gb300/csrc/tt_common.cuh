@@ -17,7 +17,7 @@ int fail(int code, const std::string& msg);
 void note_launch();  // counts kernel launches made by the library (tt_launch_count)
 
 // opt-in event profiler of tt_round's phases (tt_profile_enable / tt_profile_read)
-enum ProfClass { PROF_JACOBI = 0, PROF_QR = 1, PROF_GEMM = 2, PROF_CLASSES = 3 };
+enum ProfClass { PROF_JACOBI = 0, PROF_QR = 1, PROF_GEMM = 2, PROF_CERT = 3, PROF_CLASSES = 4 };
 bool profile_enabled();
 void profile_add(int cls, double ms, double flops);
 

@@ -329,6 +329,12 @@ int extract_rt(cudaStream_t s, const T* A, int lda, int p, int n, double* X) {
 }
 
 template <typename T>
+int copy_matrix(cudaStream_t s, const T* src, int p, int n, T* dst) {
+  TT_CUDA_CHECK(cudaMemcpyAsync(dst, src, (size_t)p * n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  return TT_OK;
+}
+
+template <typename T>
 int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out) {
   sumsq_kernel<T><<<1, 1024, 0, s>>>(a, n, out);
   TT_LAUNCH_CHECK();
@@ -344,7 +350,8 @@ int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out) {
   template int extract_r<T>(cudaStream_t, const T*, int, int, int, T*);                 \
   template int extract_rt<T>(cudaStream_t, const T*, int, int, int, double*);           \
   template int extract_r_f64<T>(cudaStream_t, const T*, int, int, int, double*);        \
-  template int frobenius_norm<T>(cudaStream_t, const T*, long long, double*);
+  template int frobenius_norm<T>(cudaStream_t, const T*, long long, double*);           \
+  template int copy_matrix<T>(cudaStream_t, const T*, int, int, T*);
 TT_EW_INST(double)
 TT_EW_INST(float)
 #undef TT_EW_INST

@@ -88,5 +88,7 @@ template <typename T>
 int extract_r_f64(cudaStream_t s, const T* A, int lda, int p, int n, double* X);
 template <typename T>
 int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out);
+template <typename T>
+int copy_matrix(cudaStream_t s, const T* src, int p, int n, T* dst);
 
 }  // namespace tt

@@ -21,8 +21,9 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda, int m, int j0,
                                                       int jb, T* __restrict__ tau,
                                                       T* __restrict__ Tm, int ldt,
-                                                      T* __restrict__ Vb, int ldv) {
+                                                      T* __restrict__ Vb, int ldv, bool staged) {
   constexpr int NW = NT / 32;
+  extern __shared__ unsigned char panel_raw[];
   __shared__ T red[NW][33];
   __shared__ T dvec[32];
   __shared__ T Ts[32][33];
@@ -30,12 +31,24 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
   __shared__ T s_sum[32];
   __shared__ int s_nz;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int mr = m - j0;
+  // the panel (rows j0..m-1, columns j0..j0+jb-1): in shared memory when it fits,
+  // column c at P + c*mr (row i at index i - j0), else read in place
+  T* P = reinterpret_cast<T*>(panel_raw);
+  auto col = [&](int c) -> T* { return staged ? (P + (int64_t)c * mr - j0) : (A + (int64_t)(j0 + c) * lda); };
+  const int64_t ld_panel = staged ? (int64_t)mr : (int64_t)lda;
+  if (staged) {
+    for (int c = 0; c < jb; ++c) {
+      const T* src = A + (int64_t)(j0 + c) * lda;
+      for (int i = j0 + tid; i < m; i += NT) P[(int64_t)c * mr + (i - j0)] = src[i];
+    }
+  }
   for (int e = tid; e < 32 * 33; e += NT) (&Ts[0][0])[e] = T(0);
   __syncthreads();
 
   for (int c = 0; c < jb; ++c) {
     const int j = j0 + c;
-    T* colj = A + (int64_t)j * lda;
+    T* colj = col(c);
     // ---- 1. norm of the part below the diagonal
     T part = T(0);
     for (int i = j + 1 + tid; i < m; i += NT) {
@@ -69,12 +82,12 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
     T acc[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] = T(0);
+    const T* c0 = col(0);
     for (int i = j + 1 + tid; i < m; i += NT) {
       const T vi = colj[i];
-      const T* row = A + (int64_t)j0 * lda + i;
 #pragma unroll
       for (int t = 0; t < 32; ++t)
-        if (t < jb) acc[t] += vi * row[(int64_t)t * lda];
+        if (t < jb) acc[t] += vi * c0[(int64_t)t * ld_panel + i];
     }
     warp_reduce_scatter32(acc, lane);
     red[warp][lane] = acc[0];
@@ -83,7 +96,7 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
       T d = T(0);
 #pragma unroll
       for (int w = 0; w < NW; ++w) d += red[w][tid];
-      if (tid < jb) d += A[(int64_t)(j0 + tid) * lda + j];
+      if (tid < jb) d += col(tid)[j];
       dvec[tid] = d;
     }
     __syncthreads();
@@ -91,10 +104,10 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
     if (tj != T(0)) {
       for (int t = c + 1; t < jb; ++t) {
         const T f = tj * dvec[t];
-        T* colt = A + (int64_t)(j0 + t) * lda;
+        T* colt = col(t);
         for (int i = j + 1 + tid; i < m; i += NT) colt[i] -= f * colj[i];
       }
-      if (tid > c && tid < jb) A[(int64_t)(j0 + tid) * lda + j] -= tj * dvec[tid];
+      if (tid > c && tid < jb) col(tid)[j] -= tj * dvec[tid];
     }
     if (tid < c) {
       T v = T(0);
@@ -107,12 +120,18 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
     }
     __syncthreads();
   }
-  // explicit unit-lower-trapezoidal V (rows j0..m-1) and T to global
+  // write back the factored panel (R above, reflectors below), the explicit
+  // unit-lower-trapezoidal V (rows j0..m-1) and T
   for (int t = 0; t < jb; ++t) {
     const int jc = j0 + t;
-    const T* src = A + (int64_t)jc * lda;
+    const T* src = col(t);
+    T* dstA = A + (int64_t)jc * lda;
     T* dst = Vb + (int64_t)jc * ldv;
-    for (int i = j0 + tid; i < m; i += NT) dst[i] = (i < jc) ? T(0) : (i == jc ? T(1) : src[i]);
+    for (int i = j0 + tid; i < m; i += NT) {
+      const T v = src[i];
+      if (staged) dstA[i] = v;
+      dst[i] = (i < jc) ? T(0) : (i == jc ? T(1) : v);
+    }
   }
   for (int e = tid; e < jb * jb; e += NT) {
     const int r = e % jb, cc = e / jb;
@@ -175,15 +194,28 @@ __global__ void init_thin_q_kernel(T* Q, int m, int p, int ldq) {
 
 }  // namespace
 
+constexpr size_t kPanelSmem = 180 * 1024;
+
 template <typename T>
 int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
+  static int configured[2] = {-1, -1};
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (configured[sizeof(T) == 8] != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(qr_panel_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPanelSmem));
+    configured[sizeof(T) == 8] = dev;
+  }
   const int p = std::min(m, n);
   const int nb = w.nb;
   int panel = 0;
   for (int j0 = 0; j0 < p; j0 += nb, ++panel) {
     const int jb = std::min(nb, p - j0);
     T* Tm = w.tmat + (int64_t)panel * nb * nb;
-    qr_panel_kernel<T, 512><<<1, 512, 0, s>>>(A, lda, m, j0, jb, w.tau, Tm, nb, w.vbuf, w.ldv);
+    const size_t panel_bytes = (size_t)(m - j0) * jb * sizeof(T);
+    const bool staged = panel_bytes <= kPanelSmem;
+    qr_panel_kernel<T, 512><<<1, 512, staged ? panel_bytes : 0, s>>>(A, lda, m, j0, jb, w.tau, Tm, nb,
+                                                                     w.vbuf, w.ldv, staged);
     TT_LAUNCH_CHECK();
     const int nt = n - (j0 + jb);
     if (nt <= 0) continue;

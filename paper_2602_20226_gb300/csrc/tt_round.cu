@@ -233,7 +233,7 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
   TT_TRY(frobenius_norm<T>(s, slot[0], cur[0] * d[0] * cur[1], B.sv.norm));
 
   // ---- 2. left-to-right truncated SVD sweep
-  int total_sweeps = 0;
+  int total_sweeps = 0, certified_bonds = 0;
   if (L > 1) {
     const double delta_scale = eps / std::sqrt((double)(L - 1));
     for (int k = 0; k < L - 1; ++k) {
@@ -267,38 +267,63 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
       }
       prof.end(pe, PROF_QR, qr_nominal(m, n));
       pe = prof.begin();
-      // one-sided Jacobi on the columns of the square factor X (p x p)
-      TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30));
-      prof.end(pe, PROF_JACOBI, 12.0 * p * (double)p * p);
-      tm.mark(5);
-      TT_TRY(svd_truncate(s, B.sv, p, p, delta_scale, max_rank));
-      int rk[2] = {0, 0};
-      TT_TRY(read_back(s, B.sv.rank, &rk[0], sizeof(int)));
-      TT_TRY(read_back(s, B.sv.sweeps, &rk[1], sizeof(int)));
-      total_sweeps += rk[1];
-      prof.flush();
-      tm.mark(6);
-      const int rn = rk[0];
-      if (rn < 1 || rn > p) return fail(TT_ERR_NUMERIC, "tt_round: invalid truncation rank");
-      // U_r (p x r') = X[:, perm[:r']] / sigma
-      pe = prof.begin();
-      TT_TRY(svd_left_vectors<T>(s, B.sv, p, rn, B.vsel));
-      if (tall) {
-        // C_k <- Q U_r (m x r', row-major);  F = U_r^T R (r' x n, row-major)
-        TT_TRY((gemm_fast<T>(s, m, rn, p, 1.0, B.Q, 1, m, B.vsel, 1, p, 0.0, slot[k], rn, 1, B.sv.status)));
-        TT_TRY((gemm_fast<T>(s, rn, n, p, 1.0, B.vsel, p, 1, B.Rbuf, 1, p, 0.0, B.F, n, 1, B.sv.status)));
+      // No truncation is possible when sigma_min > delta: then the bond keeps its rank,
+      // C_k <- Q and C_{k+1} <- R C_{k+1} represent the same tensor as the SVD factors
+      // would (they differ by an orthogonal gauge), and the SVD is skipped.
+      bool certified = false;
+      if (tall && (max_rank <= 0 || max_rank >= p) && 64 * (size_t)p <= 200 * 1024) {
+        pe = prof.begin();
+        TT_TRY(certify_full_rank(s, B.sv, B.sv.X, p, p, delta_scale));
+        prof.end(pe, PROF_CERT, (double)p * p * p / 3.0);
+        int flag = 0;
+        TT_TRY(read_back(s, B.sv.rank, &flag, sizeof(int)));
+        prof.flush();
+        certified = flag != 0;
+      }
+      int rn = p;
+      if (certified) {
+        pe = prof.begin();
+        // C_k <- Q: column-major m x p is row-major p x m; transpose into row-major m x p
+        TT_TRY(transpose_rm_to_cm<T>(s, B.Q, p, m, slot[k]));
+        // F = R (p x n, column-major) so that C_{k+1} <- R C_{k+1} below
+        TT_TRY(copy_matrix<T>(s, B.Rbuf, p, n, B.F));
+        ++certified_bonds;
       } else {
-        // F = U_r^T C_k (r' x n) from the original core, then C_k <- U_r (m x r', row-major)
-        TT_TRY((gemm_fast<T>(s, rn, n, m, 1.0, B.vsel, m, 1, slot[k], n, 1, 0.0, B.F, n, 1, B.sv.status)));
-        TT_TRY(transpose_rm_to_cm<T>(s, B.vsel, rn, m, slot[k]));
+        // one-sided Jacobi on the columns of the square factor X (p x p)
+        pe = prof.begin();
+        TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30));
+        prof.end(pe, PROF_JACOBI, 12.0 * p * (double)p * p);
+        tm.mark(5);
+        TT_TRY(svd_truncate(s, B.sv, p, p, delta_scale, max_rank));
+        int rk[2] = {0, 0};
+        TT_TRY(read_back(s, B.sv.rank, &rk[0], sizeof(int)));
+        TT_TRY(read_back(s, B.sv.sweeps, &rk[1], sizeof(int)));
+        total_sweeps += rk[1];
+        prof.flush();
+        tm.mark(6);
+        rn = rk[0];
+        if (rn < 1 || rn > p) return fail(TT_ERR_NUMERIC, "tt_round: invalid truncation rank");
+        // U_r (p x r') = X[:, perm[:r']] / sigma
+        pe = prof.begin();
+        TT_TRY(svd_left_vectors<T>(s, B.sv, p, rn, B.vsel));
+        if (tall) {
+          // C_k <- Q U_r (m x r', row-major);  F = U_r^T R (r' x n, row-major)
+          TT_TRY((gemm_fast<T>(s, m, rn, p, 1.0, B.Q, 1, m, B.vsel, 1, p, 0.0, slot[k], rn, 1, B.sv.status)));
+          TT_TRY((gemm_fast<T>(s, rn, n, p, 1.0, B.vsel, p, 1, B.Rbuf, 1, p, 0.0, B.F, n, 1, B.sv.status)));
+        } else {
+          // F = U_r^T C_k (r' x n) from the original core, then C_k <- U_r (m x r', row-major)
+          TT_TRY((gemm_fast<T>(s, rn, n, m, 1.0, B.vsel, m, 1, slot[k], n, 1, 0.0, B.F, n, 1, B.sv.status)));
+          TT_TRY(transpose_rm_to_cm<T>(s, B.vsel, rn, m, slot[k]));
+        }
       }
       const int cols = d[k + 1] * (int)cur[k + 2];
-      TT_TRY((gemm_fast<T>(s, rn, cols, n, 1.0, B.F, n, 1, slot[k + 1], cols, 1, 0.0, B.tmp, cols, 1,
-                           B.sv.status)));
+      TT_TRY((gemm_fast<T>(s, rn, cols, n, 1.0, B.F, certified ? 1 : n, certified ? p : 1, slot[k + 1],
+                           cols, 1, 0.0, B.tmp, cols, 1, B.sv.status)));
       TT_CUDA_CHECK(cudaMemcpyAsync(slot[k + 1], B.tmp, (size_t)rn * cols * sizeof(T),
                                     cudaMemcpyDeviceToDevice, s));
       prof.end(pe, PROF_GEMM,
-               (tall ? 2.0 * m * rn * p + 2.0 * rn * n * p : 2.0 * rn * n * m) + 2.0 * rn * cols * n);
+               (certified ? 0.0 : (tall ? 2.0 * m * rn * p + 2.0 * rn * n * p : 2.0 * rn * n * m)) +
+                   2.0 * rn * cols * n);
       tm.mark(7);
       cur[k + 1] = rn;
     }
@@ -311,7 +336,9 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
   for (int k = 0; k <= L; ++k) out->ranks[k] = cur[k];
   if (norm_out) *norm_out = nrm;
   if (stats) stats->jacobi_sweeps = total_sweeps;
-  if (tm.on) std::fprintf(stderr, "[tt_round trace] jacobi sweeps total=%d\n", total_sweeps);
+  if (tm.on)
+    std::fprintf(stderr, "[tt_round trace] jacobi sweeps total=%d, bonds certified full rank=%d\n",
+                 total_sweeps, certified_bonds);
   if (!std::isfinite(nrm) || (st & ST_NONFINITE)) return fail(TT_ERR_NUMERIC, "tt_round: non-finite values");
   if (st & ST_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_round: device wait expired");
   if (st & ST_NONCONVERGED) return fail(TT_ERR_NUMERIC, "tt_round: Jacobi SVD hit its sweep cap");

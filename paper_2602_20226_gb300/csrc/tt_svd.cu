@@ -32,7 +32,64 @@ __device__ __forceinline__ bool sweep_barrier(unsigned* bar, unsigned* status) {
   return grid_barrier(bar, gridDim.x, status);
 }
 
-template <int NT>
+// Columns of up to 32 * TPL rows are held in registers for the whole pair update
+// (all loads issued at once, one store pass); TPL = 0 streams longer columns.
+template <int TPL>
+__device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __restrict__ xb,
+                                            int nrow, int lane, double tol) {
+  double al = 0.0, be = 0.0, ga = 0.0;
+  double ra[TPL > 0 ? TPL : 1], rb[TPL > 0 ? TPL : 1];
+  if (TPL > 0) {
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = lane + 32 * t;
+      ra[t] = (i < nrow) ? __ldcg(xa + i) : 0.0;
+      rb[t] = (i < nrow) ? __ldcg(xb + i) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      al = fma(ra[t], ra[t], al);
+      be = fma(rb[t], rb[t], be);
+      ga = fma(ra[t], rb[t], ga);
+    }
+  } else {
+    for (int i = lane; i < nrow; i += 32) {
+      const double u = __ldcg(xa + i), v = __ldcg(xb + i);
+      al = fma(u, u, al);
+      be = fma(v, v, be);
+      ga = fma(u, v, ga);
+    }
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (!(ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                        : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t);
+  const double s = c * t;
+  if (s == 0.0) return false;  // angle below resolution: nothing to rotate
+  if (TPL > 0) {
+#pragma unroll
+    for (int q = 0; q < TPL; ++q) {
+      const int i = lane + 32 * q;
+      if (i < nrow) {
+        __stcg(xa + i, c * ra[q] - s * rb[q]);
+        __stcg(xb + i, s * ra[q] + c * rb[q]);
+      }
+    }
+  } else {
+    for (int i = lane; i < nrow; i += 32) {
+      const double u = __ldcg(xa + i), v = __ldcg(xb + i);
+      __stcg(xa + i, c * u - s * v);
+      __stcg(xb + i, s * u + c * v);
+    }
+  }
+  return true;
+}
+
+template <int NT, int TPL>
 __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int ncol, int ldx,
                                                     double tol, int max_sweeps, unsigned* bar,
                                                     unsigned* rot, unsigned* status,
@@ -63,33 +120,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
           a = b;
           b = t;
         }
-        double* xa = X + (int64_t)a * ldx;
-        double* xb = X + (int64_t)b * ldx;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int i = lane; i < nrow; i += 32) {
-          const double u = __ldcg(xa + i), v = __ldcg(xb + i);
-          al = fma(u, u, al);
-          be = fma(v, v, be);
-          ga = fma(u, v, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (fabs(zeta) > 1e150)
-                               ? 0.5 / zeta
-                               : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          const double s = c * t;
-          if (s == 0.0) continue;  // angle below resolution: nothing to rotate
-          for (int i = lane; i < nrow; i += 32) {
-            const double u = __ldcg(xa + i), v = __ldcg(xb + i);
-            __stcg(xa + i, c * u - s * v);
-            __stcg(xb + i, s * u + c * v);
-          }
-          if (lane == 0) atomicAdd(rot + sweep, 1u);
-        }
+        if (rotate_pair<TPL>(X + (int64_t)a * ldx, X + (int64_t)b * ldx, nrow, lane, tol) && lane == 0)
+          atomicAdd(rot + sweep, 1u);
       }
       if (!sweep_barrier(bar, status)) return;
     }
@@ -171,51 +203,103 @@ __global__ void svd_left_kernel(const double* X, int nrow, int ldx, const int* p
   }
 }
 
-struct CoopCfg {
-  int dev = -1;
-  int max_blocks = 0;
-};
-
-int coop_max_blocks(int threads) {
-  static CoopCfg cfg;
-  int dev = 0;
-  TT_CUDA_CHECK(cudaGetDevice(&dev));
-  if (cfg.dev != dev) {
-    int occ = 0;
-    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel<64>, threads, 0));
-    cfg.max_blocks = occ * num_sms();
-    cfg.dev = dev;
+// No-truncation certificate for an upper-triangular R (p x p, column-major, FP64):
+// sigma_min(R) >= 1 / ||R^{-1}||_F, and ||R^{-1}||_F comes from p independent
+// back substitutions (one warp per column of R^{-1}).  The computed inverse is that
+// of R + dR with |dR| <= p u |R|, so the certificate subtracts p u ||R||_F.  If
+// sigma_min > delta, no singular value can be dropped (the smallest tail already
+// exceeds delta) and the bond keeps its full rank.
+__global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int p, int ldr,
+                                                           double* colsq) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= p) return;
+  // z = R^{-1} e_j: z_j = 1/R_jj, z_i = -(sum_{l=i+1..j} R_il z_l) / R_ii for i < j,
+  // kept in this warp's slice of shared memory.
+  extern __shared__ double zbuf[];  // 8 warps x p
+  double* z = zbuf + (size_t)(threadIdx.x >> 5) * p;
+  const double rjj = R[j + (int64_t)j * ldr];
+  if (lane == 0) z[j] = 1.0 / rjj;
+  __syncwarp();
+  double nrm2 = (lane == 0) ? z[j] * z[j] : 0.0;
+  for (int i = j - 1; i >= 0; --i) {
+    double acc = 0.0;
+    for (int l = i + 1 + lane; l <= j; l += 32) acc = fma(R[i + (int64_t)l * ldr], z[l], acc);
+    acc = warp_sum(acc);
+    const double zi = -acc / R[i + (int64_t)i * ldr];
+    if (lane == 0) z[i] = zi;
+    nrm2 = fma(zi, zi, nrm2);
+    __syncwarp();
   }
-  return cfg.max_blocks;
+  if (lane == 0) colsq[j] = nrm2;
+}
+
+// flag = 1 if 1/||R^{-1}||_F - p u ||R||_F > 1.01 delta (certified full rank), else 0.
+__global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, int ldr,
+                                                       const double* colsq, const double* norm,
+                                                       double delta_scale, int* flag) {
+  __shared__ double scratch[32];
+  double inv2 = 0.0, r2 = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) inv2 += colsq[j];
+  for (int64_t e = threadIdx.x; e < (int64_t)p * p; e += blockDim.x) {
+    const int i = (int)(e % p), c = (int)(e / p);
+    if (i <= c) {
+      const double v = R[i + (int64_t)c * ldr];
+      r2 = fma(v, v, r2);
+    }
+  }
+  inv2 = block_sum(inv2, scratch);
+  r2 = block_sum(r2, scratch);
+  if (threadIdx.x == 0) {
+    const double delta = delta_scale * (*norm);
+    const double lower = (isfinite(inv2) && inv2 > 0.0) ? 1.0 / sqrt(inv2) : 0.0;
+    const double slack = (double)p * 2.220446049250313e-16 * sqrt(r2);
+    *flag = (lower - slack > 1.01 * delta) ? 1 : 0;
+  }
 }
 
 }  // namespace
 
-int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps) {
-  if (ncol <= 0 || nrow <= 0) return TT_OK;
-  if (max_sweeps > SvdWork::kMaxSweeps) max_sweeps = SvdWork::kMaxSweeps;
-  TT_CUDA_CHECK(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
-  TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
+template <int NT, int TPL>
+int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps) {
   const int npairs = (ncol + 1) / 2;
   if (ncol <= 48) {
-    jacobi_kernel<256><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, max_sweeps, w.bar, w.rot,
-                                          w.status, w.sweeps);
+    jacobi_kernel<256, TPL><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, max_sweeps, w.bar, w.rot,
+                                               w.status, w.sweeps);
     TT_LAUNCH_CHECK();
     return TT_OK;
   }
-  constexpr int NT = 64;
-  const int maxb = coop_max_blocks(NT);
-  int blocks = (int)std::min<int64_t>(ceil_div(npairs, NT / 32), maxb);
+  static int cfg_dev = -1, cfg_blocks = 0;
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (cfg_dev != dev) {
+    int occ = 0;
+    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel<NT, TPL>, NT, 0));
+    cfg_blocks = occ * num_sms();
+    cfg_dev = dev;
+  }
+  int blocks = (int)std::min<int64_t>(ceil_div(npairs, NT / 32), cfg_blocks);
   if (blocks < 1) blocks = 1;
   double* X = w.X;
   int ldx = w.ldx;
   unsigned *bar = w.bar, *rot = w.rot, *st = w.status;
   int* sw = w.sweeps;
   void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &max_sweeps, &bar, &rot, &st, &sw};
-  TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<NT>, dim3(blocks), dim3(NT),
+  TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<NT, TPL>, dim3(blocks), dim3(NT),
                                             args, 0, s));
   note_launch();
   return TT_OK;
+}
+
+int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps) {
+  if (ncol <= 0 || nrow <= 0) return TT_OK;
+  if (max_sweeps > SvdWork::kMaxSweeps) max_sweeps = SvdWork::kMaxSweeps;
+  TT_CUDA_CHECK(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
+  TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
+  if (nrow <= 128) return launch_jacobi<64, 4>(s, w, nrow, ncol, tol, max_sweeps);
+  if (nrow <= 256) return launch_jacobi<64, 8>(s, w, nrow, ncol, tol, max_sweeps);
+  if (nrow <= 512) return launch_jacobi<64, 16>(s, w, nrow, ncol, tol, max_sweeps);
+  return launch_jacobi<64, 0>(s, w, nrow, ncol, tol, max_sweeps);
 }
 
 int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
@@ -232,6 +316,24 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
   }
   svd_truncate_kernel<<<1, 1024, smem, s>>>(w.X, nrow, ncol, w.ldx, w.norm, delta_scale,
                                             (long long)max_rank, w.sigma, w.perm, w.rank, w.status);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale) {
+  static int configured = -1;
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  const size_t smem = 8 * (size_t)p * sizeof(double);
+  if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "certify_full_rank: rank too large");
+  if (configured != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+    configured = dev;
+  }
+  rinv_colnorm_kernel<<<(unsigned)ceil_div(p, 8), 256, smem, s>>>(R, p, ldr, w.sigma);
+  TT_LAUNCH_CHECK();
+  certify_kernel<<<1, 1024, 0, s>>>(R, p, ldr, w.sigma, w.norm, delta_scale, w.rank);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }

@@ -26,6 +26,11 @@ int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int m
 int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
                  int64_t max_rank);
 
+// No-truncation certificate for the upper-triangular p x p factor R (FP64, ld ldr):
+// *w.rank <- 1 if sigma_min(R) > delta = delta_scale * (*w.norm) is proven, else 0.
+// Uses w.sigma as scratch.
+int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale);
+
 // U (nrow x r, column-major) = X[:, perm[:r]] / sigma[:r]  (left singular vectors).
 template <typename TO>
 int svd_left_vectors(cudaStream_t s, const SvdWork& w, int nrow, int r, TO* U);
