@@ -139,6 +139,21 @@ size_t tt_inner_workspace_size(const tt_train* x, const tt_train* y);
 int tt_inner(const tt_train* x, const tt_train* y, double* out, void* workspace, size_t ws_bytes,
              void* stream);
 
+/* <x, y> exactly as tt_inner, for callers that cannot supply or allocate device
+ * memory: plain C programs embedding the library without a device allocator of their
+ * own, and latency-critical loops under a fixed memory budget, where cudaMalloc /
+ * cudaFree would synchronise the device.  This call takes no workspace and allocates
+ * nothing.  (The paper has no counterpart; it is an interface convenience.)
+ *   Scratch: a fixed 4 MiB device array inside the library, held by every GPU that
+ *   loads the library until the process exits.  Trains whose tt_inner_workspace_size
+ *   exceeds 4 MiB are rejected with TT_ERR_UNSUPPORTED before anything is launched.
+ *   Set-up: the first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   Sharing: all calls on a device use the same array and it keeps the last call's
+ *   contents, so calls that overlap on the GPU (other streams, other threads) race;
+ *   serialise them.  Synchronises the stream like tt_inner. */
+int tt_inner_noalloc(const tt_train* x, const tt_train* y, double* out, void* stream);
+
 /* values[s] = G_1[:, i_1^s, :] ... G_L[:, i_L^s, :]  (exact evaluation).
  *   digits  device uint8 [n][L], digit k of sample s at digits[s*L + k] (< d_k)
  *   values  device [n], x's dtype.  Asynchronous. */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "tt_round": (ctypes.c_int, [P(tt_train), f64, i64, i32, P(tt_train), P(f64), vp, sz, vp]),
     "tt_inner_workspace_size": (sz, [P(tt_train), P(tt_train)]),
     "tt_inner": (ctypes.c_int, [P(tt_train), P(tt_train), P(f64), vp, sz, vp]),
+    "tt_inner_noalloc": (ctypes.c_int, [P(tt_train), P(tt_train), P(f64), vp]),
     "tt_eval": (ctypes.c_int, [P(tt_train), vp, i64, vp, vp]),
     "tt_apply_mpo_backward": (ctypes.c_int, [P(tt_mpo), P(tt_train), P(tt_train), P(tt_mpo), P(tt_train), vp]),
     "tt_hadamard_backward": (ctypes.c_int, [P(tt_train), P(tt_train), P(tt_train), P(tt_train), P(tt_train), vp]),

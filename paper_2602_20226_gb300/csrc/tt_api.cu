@@ -338,6 +338,18 @@ int tt_inner(const tt_train* x, const tt_train* y, double* out, void* workspace,
   });
 }
 
+int tt_inner_noalloc(const tt_train* x, const tt_train* y, double* out, void* stream) {
+  return guarded([&]() -> int {
+    TT_TRY(check_train(x, "x"));
+    TT_TRY(check_train(y, "y"));
+    TT_TRY(check_same_modes(y, x->d, x->L, "y"));
+    if (y->dtype != x->dtype) return fail(TT_ERR_DTYPE, "y: dtype differs from x");
+    if (!out) return fail(TT_ERR_ARG, "tt_inner_noalloc: out is NULL");
+    g_last_error.clear();
+    return inner_noalloc(x, y, out, as_stream(stream));
+  });
+}
+
 int tt_eval(const tt_train* x, const uint8_t* digits, int64_t n, void* values, void* stream) {
   return guarded([&]() -> int {
     TT_TRY(check_train(x, "x"));

@@ -22,6 +22,9 @@ template <typename TX, typename TY>
 int inner_backward_impl(const tt_train* x, const tt_train* y, double dout, tt_train* dx,
                         tt_train* dy, void* ws, size_t ws_bytes, cudaStream_t s);
 
+// tt_inner with its scratch in a fixed device array (tt_noalloc.cu)
+int inner_noalloc(const tt_train* x, const tt_train* y, double* out, cudaStream_t s);
+
 template <typename T>
 int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values, cudaStream_t s,
               unsigned* status_dev);
