@@ -5,7 +5,7 @@ One step = y = W x (MPO apply) followed by y' = round(y, eps) on one TT, all thr
 the libtt C ABI.  Default workload: 2D quantics TT, 2 x 20 bits interleaved (L = 40),
 d = 2, rank 64 (seeded Gaussian cores), the 2D Dirichlet Laplacian MPO (rank 5,
 pre-round rank 320), eps = 1e-8, the plain FP64 form.  Alongside, the same step in the
-mixed form (FP32 cores, tensor-core GEMMs, FP64 bond SVDs), its speed-up over FP64 and
+mixed form (FP32 cores, compensated-FP32 GEMMs, FP64-finished bond SVDs), its speed-up over FP64 and
 its error against the FP64 oracle.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -219,6 +219,12 @@ def run_ours(args):
     Y32, Z32, ms32, _, _ = timed(X32, Wd32, ws32, bufs32, tt.TT_PREC_MIXED, K, Wm)
     ms_mixed = float(np.mean(ms32))
 
+    # ---- secondary workloads (reported beside the main line)
+    extra = {}
+    if not args.no_extra:
+        extra["batched"] = bench_batched(tt, dev, Wm)
+        extra["eval"] = bench_eval(tt, dev)
+
     # ---- end to end: pinned host cores in, rounded cores out, through the public API
     xh = [torch.as_tensor(c).pin_memory() for c in x_np]
     wh = [torch.as_tensor(c).pin_memory() for c in W_np]
@@ -274,12 +280,13 @@ def run_ours(args):
             "round_flops": fl_round, "apply_flops": fl_apply,
             "ranks_out_max": max(Z.ranks),
             "mixed": {"value": round(value_mixed, 4), "unit": "GFLOP/s", "ms_per_step": round(ms_mixed, 4),
-                      "dtype": "f32 cores, 3xTF32 tensor-core GEMMs, FP64 bond SVD",
+                      "dtype": "f32 cores, compensated-FP32 (Dot2) GEMMs, FP32 Jacobi + FP64 refinement, FP64 sigma/truncation/norm",
                       "speedup_vs_fp64": round(ms_step / ms_mixed, 3),
                       "rel_err_vs_fp64_oracle": err_mixed},
             "roofline": roofline,
             "e2e": {"value": round(e2e_val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(float(np.mean(e2e_ms)), 4)},
+            "secondary": extra,
             "gpu_launches": launches,
             "gpu_launches_per_step": launches // max(K, 1),
             "clocks": clocks,
@@ -289,6 +296,64 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_batched(tt, dev, warm, n_tt=64, nstreams=8):
+    """Uneven batch (L ~ U[20,60], rank ~ U[8,128], MPO rank ~ U{3,4,5}), FP32, mixed form, eps=1e-6."""
+    import torch
+
+    from paper_2602_20226_gb300 import inputs
+    from paper_2602_20226_gb300.flops import apply_flops, round_flops
+
+    shapes = inputs.batch_shapes(4, n_tt)
+    X, W = [], []
+    for i, (L, r, a) in enumerate(shapes):
+        X.append(tt.TT.from_numpy(inputs.random_tt(4000 + i, L, 2, r), device=dev, dtype=torch.float32))
+        W.append(tt.MPO.from_numpy(inputs.random_mpo(4500 + i, L, 2, a), device=dev, dtype=torch.float32))
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
+    outs = tt.tt_apply_round_batched(W, X, 1e-6, nstreams=nstreams, streams=streams)  # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    outs = tt.tt_apply_round_batched(W, X, 1e-6, nstreams=nstreams, streams=streams)
+    torch.cuda.synchronize(dev)
+    sec = time.perf_counter() - t0
+    flops = 0.0
+    for x, w, o in zip(X, W, outs):
+        yr = [a * b for a, b in zip(w.ranks, x.ranks)]
+        flops += apply_flops(w.ranks, x.ranks, x.dims) + round_flops(yr, o.ranks, x.dims)["total"]
+    return {"workload": f"{n_tt} trains, L~U[20,60], rank~U[8,128], MPO rank~U{{3,4,5}}, FP32, "
+                        f"mixed form, eps=1e-6, {nstreams} streams (host-timed, one batch)",
+            "value": round(flops / sec / 1e9, 3), "unit": "GFLOP/s", "seconds": round(sec, 3),
+            "nominal_flops": flops}
+
+
+def bench_eval(tt, dev, n=1 << 20, L=40, r=64):
+    """Evaluation at 2^20 index tuples, L = 40, rank 64, FP32 (samples/s and GFLOP/s)."""
+    import torch
+
+    from paper_2602_20226_gb300 import inputs
+    from paper_2602_20226_gb300.flops import eval_flops
+
+    x = tt.TT.from_numpy([c.astype(np.float32) for c in inputs.random_tt(230, L, 2, r)], device=dev,
+                         dtype=torch.float32)
+    dg = torch.as_tensor(inputs.random_digits(231, n, [2] * L), device=dev)
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        tt.tt_eval(x, dg, out=out)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        tt.tt_eval(x, dg, out=out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    fl = eval_flops(x.ranks, n)
+    return {"workload": f"tt_eval, {n} samples, L={L}, rank {r}, FP32", "ms": round(ms, 3),
+            "samples_per_s": round(n / (ms * 1e-3), 1), "value": round(fl / (ms * 1e-3) / 1e9, 2),
+            "unit": "GFLOP/s"}
 
 
 def cpu_baseline(x_np, W_np, eps, flops_step, repeats=2):
@@ -354,6 +419,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

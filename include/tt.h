@@ -130,6 +130,26 @@ size_t tt_round_workspace_size(const tt_train* x, int32_t prec);
 int tt_round(const tt_train* x, double eps, int64_t max_rank, int32_t prec, tt_train* out,
              double* norm_out, void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- batched apply + round over many independent trains ---- */
+
+/* Device workspace (bytes) for tt_apply_round_batched with `nstreams` streams. */
+size_t tt_apply_round_batched_workspace_size(int32_t n, const tt_mpo* W, const tt_train* x,
+                                             int32_t prec, int32_t nstreams);
+
+/* For i < n: y[i] = W[i] x[i] (tt_apply_mpo), then out[i] = round(y[i], eps, max_rank)
+ * (tt_round in form prec).  Trains may differ in length, modes and ranks.  The
+ * library's scheduler runs nstreams host worker threads, each on one caller stream
+ * and one workspace slice, taking trains largest-first (by nominal rounding work)
+ * from a shared queue, so that many latency-bound sweeps run at once.
+ *   y, out   caller-allocated outputs (y[i] sized for ranks a_k r_k; out[i] like
+ *            tt_round's output); out[i].ranks receive the rounded ranks.
+ *   streams  nstreams cudaStream_t handles (caller-owned).
+ * Returns when every train is done (all streams synchronised).  On the first failing
+ * train the remaining ones are not started and its status is returned. */
+int tt_apply_round_batched(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, double eps,
+                           int64_t max_rank, int32_t prec, tt_train* out, void* workspace,
+                           size_t ws_bytes, void* const* streams, int32_t nstreams);
+
 /* Device workspace (bytes) that tt_inner / tt_inner_backward need. */
 size_t tt_inner_workspace_size(const tt_train* x, const tt_train* y);
 

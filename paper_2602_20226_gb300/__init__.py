@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     load,
     tt_apply_mpo,
     tt_apply_mpo_backward,
+    tt_apply_round_batched,
     tt_eval,
     tt_eval_backward,
     tt_hadamard,

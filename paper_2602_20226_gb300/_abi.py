@@ -68,6 +68,9 @@ SIGNATURES = {
     "tt_inner_backward": (ctypes.c_int, [P(tt_train), P(tt_train), f64, P(tt_train), P(tt_train), vp, sz, vp]),
     "tt_eval_backward_workspace_size": (sz, [P(tt_train), i64]),
     "tt_eval_backward": (ctypes.c_int, [P(tt_train), vp, i64, vp, P(tt_train), vp, sz, vp]),
+    "tt_apply_round_batched_workspace_size": (sz, [i32, P(tt_mpo), P(tt_train), i32, i32]),
+    "tt_apply_round_batched": (ctypes.c_int, [i32, P(tt_mpo), P(tt_train), P(tt_train), f64, i64, i32,
+                                              P(tt_train), vp, sz, P(vp), i32]),
     "tt_gemm_f32": (ctypes.c_int, [i32, i32, i32, f64, vp, i64, i64, vp, i64, i64, f64, vp, i64, i64, vp]),
 }
 

@@ -270,3 +270,55 @@ def tt_eval_backward(x: TT, digits: torch.Tensor, dvalues: torch.Tensor, stream=
                                 ctypes.c_void_p(dv.data_ptr()), b.ref(), ctypes.c_void_p(ws.data_ptr()),
                                 ctypes.c_size_t(need), _stream_ptr(stream)))
     return gx
+
+
+# ---------------------------------------------------------------------------- batched
+
+
+def tt_apply_round_batched(Ws: list, xs: list, eps: float, max_rank: int = 0, prec: int | None = None,
+                           nstreams: int = 8, workspace: torch.Tensor | None = None,
+                           streams: list | None = None):
+    """Apply each W[i] to x[i] and round, for many trains at once (tt_apply_round_batched).
+
+    Returns the list of rounded TTs.  The library runs `nstreams` worker threads on as
+    many CUDA streams; every buffer comes from torch.
+    """
+    lib = load()
+    n = len(xs)
+    if n == 0:
+        return []
+    dtype, dev = xs[0].dtype, xs[0].device
+    if prec is None:
+        prec = _abi.TT_PREC_FP64 if dtype == torch.float64 else _abi.TT_PREC_MIXED
+    wd = [_desc(W) for W in Ws]
+    xd = [_desc(x) for x in xs]
+    ys, yd, ob, od = [], [], [], []
+    for W, x in zip(Ws, xs):
+        r = [a * b for a, b in zip(W.ranks, x.ranks)]
+        y = [torch.empty((r[k], x.dims[k], r[k + 1]), dtype=dtype, device=dev) for k in range(x.L)]
+        ys.append(y)
+        yd.append(_Desc(y, x.dims, r, dtype))
+        bufs = [torch.empty(c.numel(), dtype=dtype, device=dev) for c in y]
+        ob.append(bufs)
+        od.append(_Desc(bufs, x.dims, r, dtype))
+    Warr = (_abi.tt_mpo * n)(*[d.s for d in wd])
+    Xarr = (_abi.tt_train * n)(*[d.s for d in xd])
+    Yarr = (_abi.tt_train * n)(*[d.s for d in yd])
+    Oarr = (_abi.tt_train * n)(*[d.s for d in od])
+    need = int(lib.tt_apply_round_batched_workspace_size(n, Warr, Xarr, int(prec), int(nstreams)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    if streams is None:
+        streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
+    sarr = (ctypes.c_void_p * nstreams)(*[s.cuda_stream for s in streams])
+    torch.cuda.current_stream(dev).synchronize()
+    code = lib.tt_apply_round_batched(n, Warr, Xarr, Yarr, float(eps), int(max_rank), int(prec), Oarr,
+                                      ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+                                      sarr, int(nstreams))
+    _check("tt_apply_round_batched", code)
+    outs = []
+    for i, x in enumerate(xs):
+        r = [int(v) for v in Oarr[i].ranks[: x.L + 1]]
+        outs.append(TT([ob[i][k][: r[k] * x.dims[k] * r[k + 1]].view(r[k], x.dims[k], r[k + 1])
+                        for k in range(x.L)]))
+    return outs

@@ -440,6 +440,34 @@ int tt_eval_backward(const tt_train* x, const uint8_t* digits, int64_t n, const 
   });
 }
 
+size_t tt_apply_round_batched_workspace_size(int32_t n, const tt_mpo* W, const tt_train* x,
+                                             int32_t prec, int32_t nstreams) {
+  if (n <= 0 || !W || !x || nstreams < 1) return 0;
+  for (int i = 0; i < n; ++i)
+    if (check_train(&x[i], "x") != TT_OK || validate_mpo(&W[i], &x[i]) != TT_OK) return 0;
+  return batched_slice_bytes(n, W, x, prec) * (size_t)nstreams;
+}
+
+int tt_apply_round_batched(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, double eps,
+                           int64_t max_rank, int32_t prec, tt_train* out, void* workspace,
+                           size_t ws_bytes, void* const* streams, int32_t nstreams) {
+  return guarded([&]() -> int {
+    if (n < 0) return fail(TT_ERR_ARG, "tt_apply_round_batched: n < 0");
+    if (n == 0) return TT_OK;
+    if (!W || !x || !y || !out) return fail(TT_ERR_ARG, "tt_apply_round_batched: NULL descriptor array");
+    if (nstreams < 1 || !streams) return fail(TT_ERR_ARG, "tt_apply_round_batched: no streams");
+    if (!workspace) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: workspace is NULL");
+    for (int i = 0; i < n; ++i) {
+      TT_TRY(check_train(&x[i], "x"));
+      TT_TRY(validate_mpo(&W[i], &x[i]));
+      TT_TRY(validate_out(&y[i], &x[i], "y"));
+      TT_TRY(validate_out(&out[i], &x[i], "out"));
+    }
+    g_last_error.clear();
+    return apply_round_batched(n, W, x, y, eps, max_rank, prec, out, workspace, ws_bytes, streams, nstreams);
+  });
+}
+
 int tt_gemm_f32(int32_t M, int32_t N, int32_t K, double alpha, const float* A, int64_t sam,
                 int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
                 int64_t scm, int64_t scn, void* stream) {

@@ -69,6 +69,32 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// ---------------------------------------------------- thread-block cluster helpers
+// Cluster-wide barrier with release/acquire semantics, as explicit PTX with a memory
+// clobber so that no shared-memory access moves across it.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Load of `*p` from the shared memory of CTA `rank` of this cluster (distributed shared
+// memory).  Spelled out as mapa + ld.shared::cluster: a plain dereference of a mapped
+// generic pointer let the compiler schedule the load ahead of the preceding cluster
+// barrier, so CTAs read partials that their peers had not written yet.
+__device__ __forceinline__ double dsmem_load(const double* p, int rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
+__device__ __forceinline__ float dsmem_load(const float* p, int rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  float v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+  return v;
+}
+
 // Reduce-scatter of 32 values across a warp: on entry lane l holds partials v[0..31];
 // on exit v[0] of lane l holds the warp total of index l.  31 shuffles in all.
 template <typename T>

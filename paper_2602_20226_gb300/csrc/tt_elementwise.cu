@@ -246,6 +246,11 @@ __global__ void __launch_bounds__(1024) sumsq_kernel(const T* a, long long n, do
   if (threadIdx.x == 0) *out = sqrt(s);
 }
 
+__global__ void f64_to_f32_kernel(const double* a, long long n, float* b) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    b[e] = (float)a[e];
+}
+
 inline int grid_for(long long total, int per_block, int cap = 1 << 20) {
   return (int)std::max<long long>(1, std::min<long long>(ceil_div(total, per_block), cap));
 }
@@ -337,6 +342,12 @@ int copy_matrix(cudaStream_t s, const T* src, int p, int n, T* dst) {
 template <typename T>
 int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out) {
   sumsq_kernel<T><<<1, 1024, 0, s>>>(a, n, out);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+int convert_f64_to_f32(cudaStream_t s, const double* a, long long n, float* b) {
+  f64_to_f32_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(a, n, b);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }

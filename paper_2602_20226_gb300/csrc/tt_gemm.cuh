@@ -8,17 +8,29 @@
 namespace tt {
 
 // C = alpha * A B + beta * C with arbitrary element strides (see tt_gemm.cu).
-// FP64 accumulation; beta == 0 never reads C.
+// Compensated FP32 dot products (Dot2) when every operand is FP32, FP64 otherwise;
+// beta == 0 never reads C.
 template <typename TA, typename TB, typename TC>
 int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t sam, int64_t sak,
          const TB* B, int64_t sbk, int64_t sbn, double beta, TC* C, int64_t scm, int64_t scn);
 
 // FP32 GEMM on the tensor cores, TF32 with a 3-term hi/lo split (tt_gemm_tc.cu).
+// acc64: sum the per-K-block tensor-core partials in FP64 registers.
 int gemm_tf32x3(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,
                 int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
-                int64_t scm, int64_t scn, unsigned* status);
+                int64_t scm, int64_t scn, unsigned* status, bool acc64 = false);
 
-// The GEMM of each form: FP64 -> SIMT DFMA; FP32 -> tensor cores (3xTF32).
+// The GEMMs that form new cores in the sweeps: FP64 -> SIMT DFMA; FP32 -> SIMT with
+// compensated (Dot2) accumulation.  The 3xTF32 tensor-core path rounds every MMA
+// result toward zero, a bias that grows with K and shrinks the norm of the train by
+// about 1e-7 per sweep step, more than the mixed form's 1e-6 budget allows.
+template <typename T>
+int gemm_core(cudaStream_t s, int M, int N, int K, double alpha, const T* A, int64_t sam, int64_t sak,
+              const T* B, int64_t sbk, int64_t sbn, double beta, T* C, int64_t scm, int64_t scn,
+              unsigned* status);
+
+// The GEMM inside the Householder QR of each form: FP64 -> SIMT DFMA; FP32 -> SIMT
+// with compensated (Dot2) accumulation, for the same reason as gemm_core.
 template <typename T>
 int gemm_fast(cudaStream_t s, int M, int N, int K, double alpha, const T* A, int64_t sam, int64_t sak,
               const T* B, int64_t sbk, int64_t sbn, double beta, T* C, int64_t scm, int64_t scn,

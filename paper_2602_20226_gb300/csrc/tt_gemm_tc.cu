@@ -9,10 +9,12 @@
 // in tensor memory (BN FP32 columns x 128 lanes).  Per 32-wide K block, all threads
 // load the A and B tiles from global memory, split them and store hi and lo parts in
 // shared memory in the no-swizzle K-major canonical layout (8-row x 16-byte core
-// matrices); then one thread issues 3 x 4 tcgen05.mma (K = 8 each) and commits them
-// to an mbarrier.  Two shared-memory stages let the loads of block k+1 overlap the
-// MMAs of block k.  Every mbarrier wait is bounded: on expiry the kernel raises
-// ST_TIMEOUT, drains (bounded), frees its tensor memory and skips the epilogue.
+// matrices); then one thread issues 3 x 4 tcgen05.mma (K = 8 each) into a fresh
+// tensor-memory buffer and commits them to an mbarrier.  Two shared-memory stages and
+// two accumulator buffers let the loads and MMAs of block k+1 overlap the draining of
+// block k's partial into FP32 registers.  Every mbarrier wait is bounded: on expiry the
+// kernel raises ST_TIMEOUT, waits (bounded) for its MMAs, frees its tensor memory and
+// skips the epilogue.
 #include <cstdint>
 
 #include "tt_gemm.cuh"
@@ -168,12 +170,29 @@ __device__ __forceinline__ void load_split(const float* __restrict__ P, int64_t 
   }
 }
 
-template <int BN>
+// Read a finished per-block partial (BN columns of this thread's row) out of tensor
+// memory and add it into the FP32 register accumulator with round-to-nearest.
+template <int BN, typename Acc>
+__device__ __forceinline__ void drain_partial(uint32_t lane_base, Acc (&acc)[BN]) {
+#pragma unroll
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    uint32_t r[16];
+    tmem_ld16(lane_base + (uint32_t)c0, r);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[c0 + j] += (Acc)__uint_as_float(r[j]);
+  }
+}
+
+// Acc = float: block partials summed in FP32 registers (round to nearest).
+// Acc = double: block partials summed in FP64 registers, so the error of a long K is
+// that of one 32-wide block rather than of the whole FP32 accumulation.
+template <int BN, typename Acc>
 __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(TcArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int A_BYTES = TC_BM * TC_BK * 4, B_BYTES = BN * TC_BK * 4;
   constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
   constexpr uint32_t IDESC = idesc_tf32(BN);
+  constexpr uint32_t TMEM_COLS = 2 * BN;  // two accumulator buffers
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -182,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(TcArgs g) {
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -195,27 +214,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(TcArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 
+  // Each 32-wide K block accumulates into a fresh tensor-memory buffer (stage s uses
+  // buffer s, columns s*BN ..); while the MMAs of block kb run, the threads drain the
+  // partial of block kb-1 into registers.  Keeping every tensor-core accumulation chain
+  // to one K block bounds the bias of its non-round-to-nearest accumulation by the
+  // size of one block instead of the whole K; the register sums round to nearest.
+  Acc acc[BN];
+#pragma unroll
+  for (int j = 0; j < BN; ++j) acc[j] = Acc(0);
   uint32_t phase0 = 0, phase1 = 0;
-  bool pend0 = false, pend1 = false;
   bool ok = true;
   const int nkb = (g.K + TC_BK - 1) / TC_BK;
   for (int kb = 0; kb < nkb && ok; ++kb) {
     const int s = kb & 1;
-    // the stage is free once the MMAs that read it (two blocks ago) have completed
-    if (s == 0 && pend0) {
-      ok = mbar_wait(&mbar[0], phase0);
-      phase0 ^= 1;
-      pend0 = false;
-    } else if (s == 1 && pend1) {
-      ok = mbar_wait(&mbar[1], phase1);
-      phase1 ^= 1;
-      pend1 = false;
-    }
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
+    // stage s was last read by block kb-2, whose completion was awaited while draining it
     uint8_t* st = smem + s * STAGE;
     uint8_t* a_hi = st;
     uint8_t* a_lo = st + A_BYTES;
@@ -228,6 +242,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(TcArgs g) {
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+      const uint32_t dbuf = tmem + (uint32_t)(s * BN);
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 8; ++kk) {
         const uint32_t off = kk * 256;  // two core matrices along K per MMA
@@ -235,38 +250,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(TcArgs g) {
         const uint64_t dal = smem_desc(smem_u32(a_lo) + off, 128, 1024);
         const uint64_t dbh = smem_desc(smem_u32(b_hi) + off, 128, 1024);
         const uint64_t dbl = smem_desc(smem_u32(b_lo) + off, 128, 1024);
-        mma_tf32(tmem, dah, dbh, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, IDESC, 1u);
-        mma_tf32(tmem, dal, dbh, IDESC, 1u);
+        mma_tf32(dbuf, dah, dbh, IDESC, kk > 0 ? 1u : 0u);
+        mma_tf32(dbuf, dah, dbl, IDESC, 1u);
+        mma_tf32(dbuf, dal, dbh, IDESC, 1u);
       }
       mma_commit(&mbar[s]);
     }
-    if (s == 0) pend0 = true; else pend1 = true;
+    if (kb > 0) {  // drain block kb-1 from buffer s^1
+      const int sp = s ^ 1;
+      const bool w = sp == 0 ? mbar_wait(&mbar[0], phase0) : mbar_wait(&mbar[1], phase1);
+      if (sp == 0) phase0 ^= 1; else phase1 ^= 1;
+      ok = __syncthreads_and(w);
+      if (ok) {
+        tc_fence_after();
+        drain_partial<BN, Acc>(lane_base + (uint32_t)(sp * BN), acc);
+        tc_fence_before();
+      }
+    }
   }
-  // drain: wait for every outstanding commit (bounded)
-  bool drained = true;
-  if (pend0) drained = mbar_wait(&mbar[0], phase0) && drained;
-  if (pend1) drained = mbar_wait(&mbar[1], phase1) && drained;
-  ok = __syncthreads_and(ok && drained);
-  tc_fence_after();
+  // drain the last block
+  if (ok && nkb > 0) {
+    const int sp = (nkb - 1) & 1;
+    const bool w = sp == 0 ? mbar_wait(&mbar[0], phase0) : mbar_wait(&mbar[1], phase1);
+    ok = __syncthreads_and(w);
+    if (ok) {
+      tc_fence_after();
+      drain_partial<BN, Acc>(lane_base + (uint32_t)(sp * BN), acc);
+    }
+  } else if (!ok) {
+    // a wait expired: give the MMAs in flight a bounded chance to finish before freeing
+    // tensor memory (both barriers, whatever their phase)
+    mbar_wait(&mbar[0], phase0);
+    mbar_wait(&mbar[1], phase1);
+  }
 
   if (ok && nkb > 0) {
     const int row = m0 + warp * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(lane_base + (uint32_t)c0, r);
-      if (row < g.M) {
+    if (row < g.M) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < g.N) {
-            float* p = g.C + (int64_t)row * g.scm + (int64_t)col * g.scn;
-            float v = g.alpha * __uint_as_float(r[j]);
-            if (g.beta != 0.0f) v += g.beta * (*p);
-            *p = v;
-          }
+      for (int j = 0; j < BN; ++j) {
+        const int col = n0 + j;
+        if (col < g.N) {
+          float* p = g.C + (int64_t)row * g.scm + (int64_t)col * g.scn;
+          Acc v = (Acc)g.alpha * acc[j];
+          if (g.beta != 0.0f) v += (Acc)g.beta * (Acc)(*p);
+          *p = (float)v;
         }
       }
     }
@@ -274,7 +302,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(TcArgs g) {
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                  : "memory");
   }
   if (!ok && tid == 0 && g.status) atomicOr(g.status, (unsigned)ST_TIMEOUT);
@@ -285,19 +313,19 @@ constexpr size_t tc_smem_bytes() {
   return 2 * (2 * TC_BM * TC_BK * 4 + 2 * BN * TC_BK * 4);
 }
 
-template <int BN>
+template <int BN, typename Acc>
 int launch_tc(cudaStream_t s, const TcArgs& a) {
   static int configured = -1;
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {
-    TT_CUDA_CHECK(cudaFuncSetAttribute(gemm_tf32x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TT_CUDA_CHECK(cudaFuncSetAttribute(gemm_tf32x3_kernel<BN, Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tc_smem_bytes<BN>()));
     configured = dev;
   }
   dim3 grid((unsigned)ceil_div(a.N, BN), (unsigned)ceil_div(a.M, TC_BM));
   if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm_tf32x3: M too large");
-  gemm_tf32x3_kernel<BN><<<grid, TC_THREADS, tc_smem_bytes<BN>(), s>>>(a);
+  gemm_tf32x3_kernel<BN, Acc><<<grid, TC_THREADS, tc_smem_bytes<BN>(), s>>>(a);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }
@@ -306,7 +334,7 @@ int launch_tc(cudaStream_t s, const TcArgs& a) {
 
 int gemm_tf32x3(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,
                 int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
-                int64_t scm, int64_t scn, unsigned* status) {
+                int64_t scm, int64_t scn, unsigned* status, bool acc64) {
   if (M <= 0 || N <= 0) return TT_OK;
   if (K <= 0) return gemm<float, float, float>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
   // a tile is 128 rows of M: if M is short and N long, compute C^T = B^T A^T instead
@@ -321,8 +349,9 @@ int gemm_tf32x3(cudaStream_t s, int M, int N, int K, double alpha, const float* 
     std::swap(scm, scn);
   }
   TcArgs a{M, N, K, (float)alpha, (float)beta, A, sam, sak, B, sbk, sbn, C, scm, scn, status};
-  if (N <= 64) return launch_tc<64>(s, a);
-  return launch_tc<128>(s, a);
+  if (acc64) return launch_tc<64, double>(s, a);
+  if (N <= 64) return launch_tc<64, float>(s, a);
+  return launch_tc<128, float>(s, a);
 }
 
 }  // namespace tt

@@ -91,4 +91,6 @@ int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out);
 template <typename T>
 int copy_matrix(cudaStream_t s, const T* src, int p, int n, T* dst);
 
+int convert_f64_to_f32(cudaStream_t s, const double* a, long long n, float* b);
+
 }  // namespace tt

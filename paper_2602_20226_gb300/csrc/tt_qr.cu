@@ -11,7 +11,11 @@
 // Q = H_1 ... H_p [I; 0] take two launches per panel: W2 = op(T) V^T A (one CTA per
 // column, a reduction over the rows) and the rank-nb update A -= V W2 (the GEMM of
 // the form: FP64 SIMT, or tensor cores for FP32).
+#include <cooperative_groups.h>
+
 #include "tt_qr.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tt {
 
@@ -139,6 +143,148 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
   }
 }
 
+// The same panel factorisation spread over a thread-block cluster of CS CTAs: CTA c
+// keeps rows [c*chunk, (c+1)*chunk) of the panel in its shared memory; for every
+// column the partial norms and the partial dot products of the new reflector with
+// the other panel columns are combined through distributed shared memory, with two
+// cluster barriers per column (partials are double-buffered by column parity, so a
+// slot is rewritten only after every CTA has passed the next barrier).  CS SMs share
+// the panel's arithmetic, which matters most in FP64.
+template <typename T, int NT, int CS>
+__global__ void __launch_bounds__(NT) qr_panel_cluster_kernel(T* __restrict__ A, int lda, int m, int j0,
+                                                              int jb, T* __restrict__ tau,
+                                                              T* __restrict__ Tm, int ldt,
+                                                              T* __restrict__ Vb, int ldv, int chunk) {
+  constexpr int NW = NT / 32;
+  extern __shared__ unsigned char panel_raw[];
+  __shared__ T red[NW][33];
+  __shared__ T Ts[32][33];
+  __shared__ T s_sum[32];
+  __shared__ T norm_part[2], alpha_slot[2];
+  __shared__ T dot_part[2][32];
+  __shared__ T dvec[32];
+  __shared__ T s_tau, s_scal;
+  __shared__ int s_nz;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int mr = m - j0;
+  const int lo = min(mr, rank * chunk), hi = min(mr, (rank + 1) * chunk);  // local panel rows
+  T* P = reinterpret_cast<T*>(panel_raw);  // column c at P + c*chunk, local row l at index l - lo
+  auto at = [&](int c, int l) -> T& { return P[(int64_t)c * chunk + (l - lo)]; };
+  for (int c = 0; c < jb; ++c) {
+    const T* src = A + (int64_t)(j0 + c) * lda + j0;
+    for (int l = lo + tid; l < hi; l += NT) at(c, l) = src[l];
+  }
+  for (int e = tid; e < 32 * 33; e += NT) (&Ts[0][0])[e] = T(0);
+  __syncthreads();
+
+  for (int c = 0; c < jb; ++c) {
+    const int b = c & 1;
+    const int jl = c;  // local row of the diagonal element
+    const bool own = (jl >= lo && jl < hi);
+    const int r0 = max(lo, jl + 1);  // first own row below the diagonal
+    // ---- 1. partial norm below the diagonal
+    T part = T(0);
+    for (int l = r0 + tid; l < hi; l += NT) {
+      const T v = at(c, l);
+      part += v * v;
+    }
+    part = block_sum(part, s_sum);
+    if (tid == 0) {
+      norm_part[b] = part;
+      if (own) alpha_slot[b] = at(c, jl);
+    }
+    cluster_sync_all();
+    if (tid == 0) {
+      T sum = T(0);
+      for (int r = 0; r < CS; ++r) sum += dsmem_load(&norm_part[b], r);
+      const int owner = jl / chunk;
+      const T alpha = dsmem_load(&alpha_slot[b], owner);
+      if (sum == T(0)) {
+        s_tau = T(0);
+        s_scal = T(1);
+        s_nz = 0;
+      } else {
+        const T beta = -copysign(sqrt(alpha * alpha + sum), alpha);
+        s_tau = (beta - alpha) / beta;
+        s_scal = T(1) / (alpha - beta);
+        if (own) at(c, jl) = beta;
+        s_nz = 1;
+      }
+    }
+    __syncthreads();
+    const T tj = s_tau;
+    if (s_nz) {
+      const T sc = s_scal;
+      for (int l = r0 + tid; l < hi; l += NT) at(c, l) *= sc;
+    }
+    __syncthreads();
+    // ---- 2. partial d_t = [own row j] A[j, j0+t] + sum_{own rows i > j} v_i A[i, j0+t]
+    T acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = T(0);
+    for (int l = r0 + tid; l < hi; l += NT) {
+      const T vi = at(c, l);
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < jb) acc[t] += vi * P[(int64_t)t * chunk + (l - lo)];
+    }
+    warp_reduce_scatter32(acc, lane);
+    red[warp][lane] = acc[0];
+    __syncthreads();
+    if (tid < 32) {
+      T d = T(0);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) d += red[w][tid];
+      if (own && tid < jb) d += at(tid, jl);
+      dot_part[b][tid] = d;
+    }
+    cluster_sync_all();
+    if (tid < 32) {
+      T d = T(0);
+      for (int r = 0; r < CS; ++r) d += dsmem_load(&dot_part[b][tid], r);
+      dvec[tid] = d;
+    }
+    __syncthreads();
+    // ---- 3. apply H_c to the own rows of the remaining columns, extend T
+    if (tj != T(0)) {
+      for (int t = c + 1; t < jb; ++t) {
+        const T f = tj * dvec[t];
+        for (int l = r0 + tid; l < hi; l += NT) at(t, l) -= f * at(c, l);
+      }
+      if (own && tid > c && tid < jb) at(tid, jl) -= tj * dvec[tid];
+    }
+    if (tid < c) {
+      T v = T(0);
+      for (int q = tid; q < c; ++q) v += Ts[tid][q] * dvec[q];
+      Ts[tid][c] = -tj * v;
+    }
+    if (tid == 0) {
+      Ts[c][c] = tj;
+      if (rank == 0) tau[j0 + c] = tj;
+    }
+    __syncthreads();
+  }
+  // write back the own rows of the factored panel and of the explicit reflectors
+  for (int t = 0; t < jb; ++t) {
+    const int jc = j0 + t;
+    T* dstA = A + (int64_t)jc * lda + j0;
+    T* dst = Vb + (int64_t)jc * ldv + j0;
+    for (int l = lo + tid; l < hi; l += NT) {
+      const T v = at(t, l);
+      dstA[l] = v;
+      dst[l] = (l < t) ? T(0) : (l == t ? T(1) : v);
+    }
+  }
+  if (rank == 0)
+    for (int e = tid; e < jb * jb; e += NT) {
+      const int r = e % jb, cc = e / jb;
+      Tm[r + (int64_t)cc * ldt] = Ts[r][cc];
+    }
+  cluster_sync_all();  // no CTA leaves while another may still read its shared memory
+}
+
 // W2[:, c] = op(T) (V^T A[:, c]) for one column c per CTA, jb <= 32:
 // the small-M half of applying the block reflector I - V T V^T (op(T) = T^T when
 // building R, T when building Q).  V (mr x jb) and A (mr x nc) are column-major.
@@ -195,6 +341,8 @@ __global__ void init_thin_q_kernel(T* Q, int m, int p, int ldq) {
 }  // namespace
 
 constexpr size_t kPanelSmem = 180 * 1024;
+constexpr int kClusterSize = 8;       // CTAs sharing one panel
+constexpr int kClusterMinRows = 256;  // shorter panels stay on one CTA
 
 template <typename T>
 int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
@@ -204,6 +352,8 @@ int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
   if (configured[sizeof(T) == 8] != dev) {
     TT_CUDA_CHECK(cudaFuncSetAttribute(qr_panel_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kPanelSmem));
+    TT_CUDA_CHECK(cudaFuncSetAttribute(qr_panel_cluster_kernel<T, 256, kClusterSize>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
     configured[sizeof(T) == 8] = dev;
   }
   const int p = std::min(m, n);
@@ -212,14 +362,37 @@ int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
   for (int j0 = 0; j0 < p; j0 += nb, ++panel) {
     const int jb = std::min(nb, p - j0);
     T* Tm = w.tmat + (int64_t)panel * nb * nb;
-    const size_t panel_bytes = (size_t)(m - j0) * jb * sizeof(T);
-    const bool staged = panel_bytes <= kPanelSmem;
-    qr_panel_kernel<T, 512><<<1, 512, staged ? panel_bytes : 0, s>>>(A, lda, m, j0, jb, w.tau, Tm, nb,
-                                                                     w.vbuf, w.ldv, staged);
-    TT_LAUNCH_CHECK();
+    const int mr = m - j0;
+    const int chunk = (int)ceil_div(mr, kClusterSize);
+    const size_t chunk_bytes = (size_t)chunk * jb * sizeof(T);
+    if (mr >= kClusterMinRows && chunk_bytes <= kPanelSmem) {
+      // cluster panel: kClusterSize CTAs share the rows
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kClusterSize);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = chunk_bytes;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kClusterSize;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      T* tau = w.tau;
+      T* vb = w.vbuf;
+      TT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel<T, 256, kClusterSize>, A, lda, m, j0,
+                                       jb, tau, Tm, nb, vb, w.ldv, chunk));
+      note_launch();
+    } else {
+      const size_t panel_bytes = (size_t)mr * jb * sizeof(T);
+      const bool staged = panel_bytes <= kPanelSmem;
+      qr_panel_kernel<T, 512><<<1, 512, staged ? panel_bytes : 0, s>>>(A, lda, m, j0, jb, w.tau, Tm, nb,
+                                                                       w.vbuf, w.ldv, staged);
+      TT_LAUNCH_CHECK();
+    }
     const int nt = n - (j0 + jb);
     if (nt <= 0) continue;
-    const int mr = m - j0;
     const T* V = w.vbuf + j0 + (int64_t)j0 * w.ldv;
     T* At = A + j0 + (int64_t)(j0 + jb) * lda;
     // W2 = T^T (V^T At)   (jb x nt, column-major ld jb)

@@ -5,6 +5,7 @@
 // hold x's ranks), then every step rewrites slots in place.  Ranks never grow, so the
 // slots always suffice.  All scratch is carved from the caller's workspace.
 #include <chrono>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -51,6 +52,8 @@ Dims dims_of(const tt_train* x) {
 template <typename T>
 struct Bufs {
   T *A = nullptr, *Q = nullptr, *tmp = nullptr, *Rbuf = nullptr, *vsel = nullptr, *F = nullptr;
+  float *X32 = nullptr, *V32 = nullptr;  // mixed-form bond SVD
+  double* W64 = nullptr;
   QrWork<T> qr;
   SvdWork sv;
 };
@@ -70,6 +73,11 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   B.vsel = c.take<T>((size_t)D.r_max * D.r_max);
   B.F = c.take<T>((size_t)D.r_max * D.r_max);
   B.sv.X = c.take<double>((size_t)D.r_max * D.r_max);
+  if (std::is_same<T, float>::value) {
+    B.X32 = c.take<float>((size_t)D.r_max * D.r_max);
+    B.V32 = c.take<float>((size_t)D.r_max * D.r_max);
+    B.W64 = c.take<double>((size_t)D.r_max * D.r_max);
+  }
   B.sv.sigma = c.take<double>(D.r_max);
   B.sv.perm = c.take<int>(D.r_max);
   B.sv.rank = c.take<int>(1);
@@ -85,6 +93,10 @@ template <typename T>
 int panel_width() {
   return sizeof(T) == 8 ? 16 : 32;
 }
+
+// Column-orthogonality tolerance of the FP64 sweeps that finish a mixed-form bond SVD
+// (times sqrt(p)): far below the FP32 rounding of the cores that the factors go into.
+constexpr double kMixedRefineTol = 1.0 / (1 << 30);
 
 template <typename T>
 double jacobi_tol(int nrow) {
@@ -222,7 +234,7 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
     const int rows = (int)cur[k - 1] * d[k - 1];
     // C_{k-1} <- C_{k-1} R^T
     pe = prof.begin();
-    TT_TRY((gemm_fast<T>(s, rows, p, n, 1.0, slot[k - 1], n, 1, B.Rbuf, p, 1, 0.0, B.tmp, p, 1,
+    TT_TRY((gemm_core<T>(s, rows, p, n, 1.0, slot[k - 1], n, 1, B.Rbuf, p, 1, 0.0, B.tmp, p, 1,
                          B.sv.status)));
     prof.end(pe, PROF_GEMM, 2.0 * rows * p * n);
     TT_CUDA_CHECK(cudaMemcpyAsync(slot[k - 1], B.tmp, (size_t)rows * p * sizeof(T),
@@ -273,7 +285,8 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
       bool certified = false;
       if (tall && (max_rank <= 0 || max_rank >= p) && 64 * (size_t)p <= 200 * 1024) {
         pe = prof.begin();
-        TT_TRY(certify_full_rank(s, B.sv, B.sv.X, p, p, delta_scale));
+        TT_TRY(certify_full_rank(s, B.sv, B.sv.X, p, p, delta_scale,
+                                 sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07));
         prof.end(pe, PROF_CERT, (double)p * p * p / 3.0);
         int flag = 0;
         TT_TRY(read_back(s, B.sv.rank, &flag, sizeof(int)));
@@ -289,9 +302,26 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         TT_TRY(copy_matrix<T>(s, B.Rbuf, p, n, B.F));
         ++certified_bonds;
       } else {
-        // one-sided Jacobi on the columns of the square factor X (p x p)
         pe = prof.begin();
-        TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30));
+        int sweeps32 = 0;
+        const bool mixed_svd = std::is_same<T, float>::value && jacobi_block_smem(p, p) <= 200 * 1024;
+        if (mixed_svd) {
+          // Mixed form: FP32 one-sided Jacobi with accumulated rotations V (block
+          // round-robin) does the bulk of the diagonalisation; W = X V is re-formed in
+          // FP64 and finished by FP64 one-sided Jacobi sweeps.  W's columns are already
+          // orthogonal to the FP32 tolerance, so the FP64 sweeps converge in one or two
+          // (quadratic convergence), and sigma, the truncation decision and U are FP64.
+          TT_TRY(convert_f64_to_f32(s, B.sv.X, (int64_t)p * p, B.X32));
+          TT_TRY(jacobi_block_f32(s, B.sv, B.X32, p, p, p, B.V32, p, 30));
+          if (tm.on) TT_TRY(read_back(s, B.sv.sweeps, &sweeps32, sizeof(int)));
+          TT_TRY((gemm<double, float, double>(s, p, p, p, 1.0, B.sv.X, 1, p, B.V32, 1, p, 0.0, B.W64, 1, p)));
+          TT_CUDA_CHECK(cudaMemcpyAsync(B.sv.X, B.W64, (size_t)p * p * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+          TT_TRY(jacobi_svd(s, B.sv, p, p, kMixedRefineTol * std::sqrt((double)p), 30, delta_scale));
+        } else {
+          // one-sided Jacobi on the columns of the square factor X (p x p)
+          TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30, delta_scale));
+        }
         prof.end(pe, PROF_JACOBI, 12.0 * p * (double)p * p);
         tm.mark(5);
         TT_TRY(svd_truncate(s, B.sv, p, p, delta_scale, max_rank));
@@ -302,22 +332,25 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         prof.flush();
         tm.mark(6);
         rn = rk[0];
+        if (tm.on)
+          std::fprintf(stderr, "[tt_round trace] bond %d p=%d sweeps32=%d sweeps64=%d rank=%d\n", k, p,
+                       sweeps32, rk[1], rn);
         if (rn < 1 || rn > p) return fail(TT_ERR_NUMERIC, "tt_round: invalid truncation rank");
         // U_r (p x r') = X[:, perm[:r']] / sigma
         pe = prof.begin();
         TT_TRY(svd_left_vectors<T>(s, B.sv, p, rn, B.vsel));
         if (tall) {
           // C_k <- Q U_r (m x r', row-major);  F = U_r^T R (r' x n, row-major)
-          TT_TRY((gemm_fast<T>(s, m, rn, p, 1.0, B.Q, 1, m, B.vsel, 1, p, 0.0, slot[k], rn, 1, B.sv.status)));
-          TT_TRY((gemm_fast<T>(s, rn, n, p, 1.0, B.vsel, p, 1, B.Rbuf, 1, p, 0.0, B.F, n, 1, B.sv.status)));
+          TT_TRY((gemm_core<T>(s, m, rn, p, 1.0, B.Q, 1, m, B.vsel, 1, p, 0.0, slot[k], rn, 1, B.sv.status)));
+          TT_TRY((gemm_core<T>(s, rn, n, p, 1.0, B.vsel, p, 1, B.Rbuf, 1, p, 0.0, B.F, n, 1, B.sv.status)));
         } else {
           // F = U_r^T C_k (r' x n) from the original core, then C_k <- U_r (m x r', row-major)
-          TT_TRY((gemm_fast<T>(s, rn, n, m, 1.0, B.vsel, m, 1, slot[k], n, 1, 0.0, B.F, n, 1, B.sv.status)));
+          TT_TRY((gemm_core<T>(s, rn, n, m, 1.0, B.vsel, m, 1, slot[k], n, 1, 0.0, B.F, n, 1, B.sv.status)));
           TT_TRY(transpose_rm_to_cm<T>(s, B.vsel, rn, m, slot[k]));
         }
       }
       const int cols = d[k + 1] * (int)cur[k + 2];
-      TT_TRY((gemm_fast<T>(s, rn, cols, n, 1.0, B.F, certified ? 1 : n, certified ? p : 1, slot[k + 1],
+      TT_TRY((gemm_core<T>(s, rn, cols, n, 1.0, B.F, certified ? 1 : n, certified ? p : 1, slot[k + 1],
                            cols, 1, 0.0, B.tmp, cols, 1, B.sv.status)));
       TT_CUDA_CHECK(cudaMemcpyAsync(slot[k + 1], B.tmp, (size_t)rn * cols * sizeof(T),
                                     cudaMemcpyDeviceToDevice, s));

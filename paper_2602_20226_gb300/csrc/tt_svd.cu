@@ -36,7 +36,7 @@ __device__ __forceinline__ bool sweep_barrier(unsigned* bar, unsigned* status) {
 // (all loads issued at once, one store pass); TPL = 0 streams longer columns.
 template <int TPL>
 __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __restrict__ xb,
-                                            int nrow, int lane, double tol) {
+                                            int nrow, int lane, double tol, double negl) {
   double al = 0.0, be = 0.0, ga = 0.0;
   double ra[TPL > 0 ? TPL : 1], rb[TPL > 0 ? TPL : 1];
   if (TPL > 0) {
@@ -63,6 +63,7 @@ __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __r
   al = warp_sum(al);
   be = warp_sum(be);
   ga = warp_sum(ga);
+  if (al < negl && be < negl) return false;  // both columns are truncated whatever the angle
   if (!(ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
   const double zeta = (be - al) / (2.0 * ga);
   const double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
@@ -91,10 +92,12 @@ __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __r
 
 template <int NT, int TPL>
 __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int ncol, int ldx,
-                                                    double tol, int max_sweeps, unsigned* bar,
-                                                    unsigned* rot, unsigned* status,
-                                                    int* sweeps_out) {
+                                                    double tol, double negl_scale, const double* norm,
+                                                    int max_sweeps, unsigned* bar, unsigned* rot,
+                                                    unsigned* status, int* sweeps_out) {
   constexpr int WPB = NT / 32;
+  const double nl = negl_scale > 0.0 ? negl_scale * __ldcg(norm) : 0.0;
+  const double negl = nl * nl;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * WPB + (threadIdx.x >> 5);
   const int GW = gridDim.x * WPB;
@@ -120,7 +123,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
           a = b;
           b = t;
         }
-        if (rotate_pair<TPL>(X + (int64_t)a * ldx, X + (int64_t)b * ldx, nrow, lane, tol) && lane == 0)
+        if (rotate_pair<TPL>(X + (int64_t)a * ldx, X + (int64_t)b * ldx, nrow, lane, tol, negl) &&
+            lane == 0)
           atomicAdd(rot + sweep, 1u);
       }
       if (!sweep_barrier(bar, status)) return;
@@ -130,6 +134,138 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *sweeps_out = sweep;
     if (!converged) atomicOr(status, (unsigned)ST_NONCONVERGED);
+  }
+}
+
+// FP32 one-sided Jacobi with accumulated rotations, organised as a block round-robin:
+// the columns are cut into groups of 16; in each outer round a CTA takes one pair of
+// groups (32 columns of X and of V) into shared memory and sweeps all pairs among
+// them (31 inner rounds of 16 rotations, one warp per pair, __syncthreads between
+// inner rounds), then writes them back.  Group pairs follow the round-robin order,
+// so a grid barrier is needed only between outer rounds: 2G - 1 per sweep for G
+// groups instead of p - 1.  The mixed form uses it as the fast part of its bond SVD.
+constexpr int kJbGroup = 16;
+
+__global__ void __launch_bounds__(512) jacobi_block_f32_kernel(float* X, int nrow, int ncol, int ldx,
+                                                                float* V, int ldv, float tol,
+                                                                int max_sweeps, unsigned* bar,
+                                                                unsigned* rot, unsigned* status,
+                                                                int* sweeps_out) {
+  extern __shared__ float jsm[];
+  constexpr int C2 = 2 * kJbGroup;
+  float* Xs = jsm;                           // C2 columns x nrow
+  float* Vs = jsm + (size_t)C2 * nrow;       // C2 columns x ncol
+  __shared__ int cols[C2];
+  __shared__ unsigned s_rot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = (ncol + kJbGroup - 1) / kJbGroup;
+  const int NG = G + (G & 1);
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int r = 0; r < NG - 1; ++r) {
+      for (int q = blockIdx.x; q < NG / 2; q += gridDim.x) {
+        int ga, gb;
+        if (q == 0) {
+          ga = r;
+          gb = NG - 1;
+        } else {
+          ga = (r + q) % (NG - 1);
+          gb = (r - q + NG - 1) % (NG - 1);
+        }
+        if (tid < C2) {
+          const int g = tid < kJbGroup ? ga : gb;
+          const int c = g * kJbGroup + (tid % kJbGroup);
+          cols[tid] = (g < G && c < ncol) ? c : -1;
+        }
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int e = tid; e < C2 * nrow; e += blockDim.x) {
+          const int c = e / nrow, i = e % nrow;
+          Xs[e] = cols[c] >= 0 ? __ldcg(X + i + (int64_t)cols[c] * ldx) : 0.f;
+        }
+        for (int e = tid; e < C2 * ncol; e += blockDim.x) {
+          const int c = e / ncol, i = e % ncol;
+          Vs[e] = cols[c] >= 0 ? __ldcg(V + i + (int64_t)cols[c] * ldv) : 0.f;
+        }
+        __syncthreads();
+        // inner round-robin over the 32 local slots: 31 rounds x 16 pairs
+        unsigned local = 0;
+        for (int ir = 0; ir < C2 - 1; ++ir) {
+          int a, b;
+          if (warp == 0) {
+            a = ir;
+            b = C2 - 1;
+          } else {
+            a = (ir + warp) % (C2 - 1);
+            b = (ir - warp + C2 - 1) % (C2 - 1);
+          }
+          if (cols[a] >= 0 && cols[b] >= 0) {
+            float* xa = Xs + (size_t)a * nrow;
+            float* xb = Xs + (size_t)b * nrow;
+            float al = 0.f, be = 0.f, ga = 0.f;
+            for (int i = lane; i < nrow; i += 32) {
+              const float u = xa[i], v = xb[i];
+              al = fmaf(u, u, al);
+              be = fmaf(v, v, be);
+              ga = fmaf(u, v, ga);
+            }
+            al = warp_sum(al);
+            be = warp_sum(be);
+            ga = warp_sum(ga);
+            if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+              const float zeta = (be - al) / (2.f * ga);
+              const float t = (fabsf(zeta) > 1e18f) ? 0.5f / zeta
+                                                    : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+              const float c = 1.f / sqrtf(1.f + t * t);
+              const float s = c * t;
+              if (s != 0.f) {
+                for (int i = lane; i < nrow; i += 32) {
+                  const float u = xa[i], v = xb[i];
+                  xa[i] = c * u - s * v;
+                  xb[i] = s * u + c * v;
+                }
+                float* va = Vs + (size_t)a * ncol;
+                float* vb = Vs + (size_t)b * ncol;
+                for (int i = lane; i < ncol; i += 32) {
+                  const float u = va[i], v = vb[i];
+                  va[i] = c * u - s * v;
+                  vb[i] = s * u + c * v;
+                }
+                ++local;
+              }
+            }
+          }
+          __syncthreads();
+        }
+        if (lane == 0 && local) atomicAdd(&s_rot, local);
+        for (int e = tid; e < C2 * nrow; e += blockDim.x) {
+          const int c = e / nrow, i = e % nrow;
+          if (cols[c] >= 0) __stcg(X + i + (int64_t)cols[c] * ldx, Xs[e]);
+        }
+        for (int e = tid; e < C2 * ncol; e += blockDim.x) {
+          const int c = e / ncol, i = e % ncol;
+          if (cols[c] >= 0) __stcg(V + i + (int64_t)cols[c] * ldv, Vs[e]);
+        }
+        __syncthreads();
+        if (tid == 0 && s_rot) atomicAdd(rot + sweep, s_rot);
+      }
+      if (!sweep_barrier(bar, status)) return;
+    }
+    converged = (*(volatile unsigned*)(rot + sweep) == 0u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *sweeps_out = sweep;
+    if (!converged) atomicOr(status, (unsigned)ST_NONCONVERGED);
+  }
+}
+
+__global__ void identity_f32_kernel(float* V, int n, int ldv) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), c = (int)(e / n);
+    V[i + (int64_t)c * ldv] = (i == c) ? 1.f : 0.f;
   }
 }
 
@@ -237,7 +373,7 @@ __global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int 
 // flag = 1 if 1/||R^{-1}||_F - p u ||R||_F > 1.01 delta (certified full rank), else 0.
 __global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, int ldr,
                                                        const double* colsq, const double* norm,
-                                                       double delta_scale, int* flag) {
+                                                       double delta_scale, double unit, int* flag) {
   __shared__ double scratch[32];
   double inv2 = 0.0, r2 = 0.0;
   for (int j = threadIdx.x; j < p; j += blockDim.x) inv2 += colsq[j];
@@ -253,7 +389,7 @@ __global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, i
   if (threadIdx.x == 0) {
     const double delta = delta_scale * (*norm);
     const double lower = (isfinite(inv2) && inv2 > 0.0) ? 1.0 / sqrt(inv2) : 0.0;
-    const double slack = (double)p * 2.220446049250313e-16 * sqrt(r2);
+    const double slack = (double)p * unit * sqrt(r2);
     *flag = (lower - slack > 1.01 * delta) ? 1 : 0;
   }
 }
@@ -261,11 +397,12 @@ __global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, i
 }  // namespace
 
 template <int NT, int TPL>
-int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps) {
+int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, double negl_scale,
+                  int max_sweeps) {
   const int npairs = (ncol + 1) / 2;
   if (ncol <= 48) {
-    jacobi_kernel<256, TPL><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, max_sweeps, w.bar, w.rot,
-                                               w.status, w.sweeps);
+    jacobi_kernel<256, TPL><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, negl_scale, w.norm, max_sweeps,
+                                               w.bar, w.rot, w.status, w.sweeps);
     TT_LAUNCH_CHECK();
     return TT_OK;
   }
@@ -282,24 +419,30 @@ int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, in
   if (blocks < 1) blocks = 1;
   double* X = w.X;
   int ldx = w.ldx;
+  const double* nrm = w.norm;
   unsigned *bar = w.bar, *rot = w.rot, *st = w.status;
   int* sw = w.sweeps;
-  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &max_sweeps, &bar, &rot, &st, &sw};
+  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &negl_scale, &nrm, &max_sweeps, &bar, &rot, &st, &sw};
   TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<NT, TPL>, dim3(blocks), dim3(NT),
                                             args, 0, s));
   note_launch();
   return TT_OK;
 }
 
-int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps) {
+int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps,
+               double delta_scale) {
+  // A column with ||x||^2 < delta^2 / (2 ncol) is truncated even after any rotation
+  // among such columns (all of them together hold less than delta^2 / 2), so pairs of
+  // two such columns are left alone; delta_scale = 0 rotates every pair.
+  const double negl_scale = delta_scale > 0.0 ? delta_scale / std::sqrt(2.0 * std::max(ncol, 1)) : 0.0;
   if (ncol <= 0 || nrow <= 0) return TT_OK;
   if (max_sweeps > SvdWork::kMaxSweeps) max_sweeps = SvdWork::kMaxSweeps;
   TT_CUDA_CHECK(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
   TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
-  if (nrow <= 128) return launch_jacobi<64, 4>(s, w, nrow, ncol, tol, max_sweeps);
-  if (nrow <= 256) return launch_jacobi<64, 8>(s, w, nrow, ncol, tol, max_sweeps);
-  if (nrow <= 512) return launch_jacobi<64, 16>(s, w, nrow, ncol, tol, max_sweeps);
-  return launch_jacobi<64, 0>(s, w, nrow, ncol, tol, max_sweeps);
+  if (nrow <= 128) return launch_jacobi<64, 4>(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
+  if (nrow <= 256) return launch_jacobi<64, 8>(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
+  if (nrow <= 512) return launch_jacobi<64, 16>(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
+  return launch_jacobi<64, 0>(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
 }
 
 int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
@@ -320,7 +463,8 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
   return TT_OK;
 }
 
-int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale) {
+int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale,
+                      double unit) {
   static int configured = -1;
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
@@ -333,8 +477,49 @@ int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ld
   }
   rinv_colnorm_kernel<<<(unsigned)ceil_div(p, 8), 256, smem, s>>>(R, p, ldr, w.sigma);
   TT_LAUNCH_CHECK();
-  certify_kernel<<<1, 1024, 0, s>>>(R, p, ldr, w.sigma, w.norm, delta_scale, w.rank);
+  certify_kernel<<<1, 1024, 0, s>>>(R, p, ldr, w.sigma, w.norm, delta_scale, unit, w.rank);
   TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+size_t jacobi_block_smem(int nrow, int ncol) {
+  return (size_t)2 * kJbGroup * ((size_t)nrow + ncol) * sizeof(float);
+}
+
+int jacobi_block_f32(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, int ldx, float* V, int ldv,
+                     int max_sweeps) {
+  if (ncol <= 0 || nrow <= 0) return TT_OK;
+  const size_t smem = jacobi_block_smem(nrow, ncol);
+  if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "jacobi_block_f32: factor too large");
+  if (max_sweeps > SvdWork::kMaxSweeps) max_sweeps = SvdWork::kMaxSweeps;
+  static int cfg_dev = -1, cfg_blocks = 0;
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (cfg_dev != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(jacobi_block_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+    int occ = 0;
+    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_block_f32_kernel, 512,
+                                                                200 * 1024));
+    cfg_blocks = std::max(1, occ) * num_sms();
+    cfg_dev = dev;
+  }
+  identity_f32_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)ncol * ncol, 256), 4096), 256, 0, s>>>(
+      V, ncol, ldv);
+  TT_LAUNCH_CHECK();
+  TT_CUDA_CHECK(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
+  TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
+  const int G = (ncol + kJbGroup - 1) / kJbGroup;
+  const int NG = G + (G & 1);
+  int blocks = std::min(NG / 2, cfg_blocks);
+  if (blocks < 1) blocks = 1;
+  const float tol = std::sqrt((float)std::max(nrow, 1)) * 5.9604645e-8f;
+  unsigned *bar = w.bar, *rot = w.rot, *st = w.status;
+  int* sw = w.sweeps;
+  void* args[] = {&X, &nrow, &ncol, &ldx, &V, &ldv, (void*)&tol, &max_sweeps, &bar, &rot, &st, &sw};
+  TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_block_f32_kernel, dim3(blocks), dim3(512),
+                                            args, smem, s));
+  note_launch();
   return TT_OK;
 }
 

@@ -20,16 +20,27 @@ struct SvdWork {
 };
 
 // One-sided Jacobi on the columns of X (nrow x ncol); the rotations are not kept.
-int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps);
+// delta_scale > 0: pairs of columns that the truncation at delta = delta_scale * (*norm)
+// discards in any case are skipped.
+int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps,
+               double delta_scale = 0.0);
+
+// FP32 one-sided Jacobi with accumulated rotations (V = I on entry is set here), block
+// round-robin in shared memory; the fast part of the mixed form's bond SVD.
+size_t jacobi_block_smem(int nrow, int ncol);
+int jacobi_block_f32(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, int ldx, float* V, int ldv,
+                     int max_sweeps);
 
 // sigma, perm and the truncation rank with delta = delta_scale * (*norm).
 int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
                  int64_t max_rank);
 
 // No-truncation certificate for the upper-triangular p x p factor R (FP64, ld ldr):
-// *w.rank <- 1 if sigma_min(R) > delta = delta_scale * (*w.norm) is proven, else 0.
-// Uses w.sigma as scratch.
-int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale);
+// *w.rank <- 1 if sigma_min(R) > delta = delta_scale * (*w.norm) is proven, else 0;
+// `unit` is the unit roundoff R was computed in (the certificate allows p*unit*||R||_F
+// of error in R).  Uses w.sigma as scratch.
+int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale,
+                      double unit);
 
 // U (nrow x r, column-major) = X[:, perm[:r]] / sigma[:r]  (left singular vectors).
 template <typename TO>
