@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MPO·TT apply+round GFLOP/s & % tensor peak, mixed vs FP64 GPU, rel err ≤1e-6"
+MIXED_EPS = 1e-6
 WORKLOAD = {
     "workload": "2D quantics TT L=40 (2x20 bits interleaved), d=2, rank 64, 2D Dirichlet Laplacian "
                 "MPO rank 5 (n=320), apply + tt_round eps=1e-8",
@@ -144,14 +145,14 @@ def run_ours(args):
         bufs = [torch.empty(c.numel(), dtype=tdt, device=dev) for c in Y0.cores]
         return x_np, W_np, X, W, ws, bufs
 
-    def step(X, W, ws, bufs, prec):
+    def step(X, W, ws, bufs, prec, e=None):
         Y = tt.tt_apply_mpo(W, X)
-        Z, _ = tt.tt_round(Y, eps, 0, prec, workspace=ws, out_buffers=bufs)
+        Z, _ = tt.tt_round(Y, eps if e is None else e, 0, prec, workspace=ws, out_buffers=bufs)
         return Y, Z
 
-    def timed(X, W, ws, bufs, prec, K, Wm):
+    def timed(X, W, ws, bufs, prec, K, Wm, e=None):
         for _ in range(Wm):
-            step(X, W, ws, bufs, prec)
+            step(X, W, ws, bufs, prec, e)
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
@@ -164,7 +165,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            Y, Z = step(X, W, ws, bufs, prec)
+            Y, Z = step(X, W, ws, bufs, prec, e)
             e1.record(stream)
             e1.synchronize()
             ms_steps.append(e0.elapsed_time(e1))
@@ -214,15 +215,18 @@ def run_ours(args):
                    for k, v in prof.items()},
     }
 
-    # ---- mixed form on the same TT shape (FP32 cores)
+    # ---- mixed form on the same TT shape (FP32 cores) against the FP64 form, both at
+    # eps = 1e-6 (FP32 factors cannot resolve the 1e-8 of the main line)
+    _, _, ms64m, _, _ = timed(X, W, ws, bufs, tt.TT_PREC_FP64, K, Wm, MIXED_EPS)
+    ms_fp64_same_eps = float(np.mean(ms64m))
     x32, W32, X32, Wd32, ws32, bufs32 = make("f32")
-    Y32, Z32, ms32, _, _ = timed(X32, Wd32, ws32, bufs32, tt.TT_PREC_MIXED, K, Wm)
+    Y32, Z32, ms32, _, _ = timed(X32, Wd32, ws32, bufs32, tt.TT_PREC_MIXED, K, Wm, MIXED_EPS)
     ms_mixed = float(np.mean(ms32))
 
     # ---- secondary workloads (reported beside the main line)
     extra = {}
     if not args.no_extra:
-        extra["batched"] = bench_batched(tt, dev, Wm)
+        extra["batched"] = bench_batched(tt, dev, Wm, n_tt=args.batch_trains)
         extra["eval"] = bench_eval(tt, dev)
 
     # ---- end to end: pinned host cores in, rounded cores out, through the public API
@@ -253,7 +257,8 @@ def run_ours(args):
         dist.all_reduce(tt_, op=dist.ReduceOp.MAX)
         t_max = float(tt_.item())
     value = world * flops_step / (t_max * 1e-3) / 1e9
-    value_mixed = flops_step / (ms_mixed * 1e-3) / 1e9
+    flops_mixed = fl_apply + round_flops(Y32.ranks, Z32.ranks, X.dims)["total"]
+    value_mixed = flops_mixed / (ms_mixed * 1e-3) / 1e9
     e2e_val = world * flops_step / (float(np.mean(e2e_ms)) * 1e-3) / 1e9
 
     err_mixed = None
@@ -263,7 +268,7 @@ def run_ours(args):
 
         # accuracy of the mixed form against the FP64 oracle on the same FP32 inputs
         y32 = [c.astype(np.float64) for c in Y32.numpy()]
-        ref32 = ocore.round_tt(y32, eps)
+        ref32 = ocore.round_tt(y32, MIXED_EPS)
         err_mixed = ocore.rel_err(Z32.numpy(), ref32)
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(x_np, W_np, eps, flops_step)
@@ -280,8 +285,9 @@ def run_ours(args):
             "round_flops": fl_round, "apply_flops": fl_apply,
             "ranks_out_max": max(Z.ranks),
             "mixed": {"value": round(value_mixed, 4), "unit": "GFLOP/s", "ms_per_step": round(ms_mixed, 4),
-                      "dtype": "f32 cores, compensated-FP32 (Dot2) GEMMs, FP32 Jacobi + FP64 refinement, FP64 sigma/truncation/norm",
-                      "speedup_vs_fp64": round(ms_step / ms_mixed, 3),
+                      "eps": MIXED_EPS, "fp64_ms_per_step_same_eps": round(ms_fp64_same_eps, 4),
+                      "dtype": "f32 cores, compensated-FP32 (Dot2) GEMMs, FP32 Jacobi with FP64 sigma/truncation/norm",
+                      "speedup_vs_fp64": round(ms_fp64_same_eps / ms_mixed, 3),
                       "rel_err_vs_fp64_oracle": err_mixed},
             "roofline": roofline,
             "e2e": {"value": round(e2e_val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
@@ -298,33 +304,51 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def bench_batched(tt, dev, warm, n_tt=64, nstreams=8):
-    """Uneven batch (L ~ U[20,60], rank ~ U[8,128], MPO rank ~ U{3,4,5}), FP32, mixed form, eps=1e-6."""
+def bench_batched(tt, dev, warm, n_tt=64, nstreams=8, n_err=4):
+    """Uneven batch (L ~ U[20,60], rank ~ U[8,128], MPO rank ~ U{3,4,5}), eps = 1e-6, through
+    tt_apply_round_batched: the mixed form (FP32 cores) against the FP64 form on the same
+    trains, and the mixed results' error against the oracle on the n_err cheapest trains."""
     import torch
 
+    from oracle import core as ocore
     from paper_2602_20226_gb300 import inputs
     from paper_2602_20226_gb300.flops import apply_flops, round_flops
 
     shapes = inputs.batch_shapes(4, n_tt)
-    X, W = [], []
-    for i, (L, r, a) in enumerate(shapes):
-        X.append(tt.TT.from_numpy(inputs.random_tt(4000 + i, L, 2, r), device=dev, dtype=torch.float32))
-        W.append(tt.MPO.from_numpy(inputs.random_mpo(4500 + i, L, 2, a), device=dev, dtype=torch.float32))
+    xs = [inputs.random_tt(4000 + i, L, 2, r) for i, (L, r, a) in enumerate(shapes)]
+    ws = [inputs.random_mpo(4500 + i, L, 2, a) for i, (L, r, a) in enumerate(shapes)]
     streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
-    outs = tt.tt_apply_round_batched(W, X, 1e-6, nstreams=nstreams, streams=streams)  # warm-up
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    outs = tt.tt_apply_round_batched(W, X, 1e-6, nstreams=nstreams, streams=streams)
-    torch.cuda.synchronize(dev)
-    sec = time.perf_counter() - t0
-    flops = 0.0
-    for x, w, o in zip(X, W, outs):
-        yr = [a * b for a, b in zip(w.ranks, x.ranks)]
-        flops += apply_flops(w.ranks, x.ranks, x.dims) + round_flops(yr, o.ranks, x.dims)["total"]
-    return {"workload": f"{n_tt} trains, L~U[20,60], rank~U[8,128], MPO rank~U{{3,4,5}}, FP32, "
-                        f"mixed form, eps=1e-6, {nstreams} streams (host-timed, one batch)",
-            "value": round(flops / sec / 1e9, 3), "unit": "GFLOP/s", "seconds": round(sec, 3),
-            "nominal_flops": flops}
+    res = {}
+    outs_by_form = {}
+    for form, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
+        X = [tt.TT.from_numpy([c.astype(np.float32) for c in x], device=dev, dtype=dt) for x in xs]
+        W = [tt.MPO.from_numpy([c.astype(np.float32) for c in w], device=dev, dtype=dt) for w in ws]
+        outs = tt.tt_apply_round_batched(W, X, 1e-6, nstreams=nstreams, streams=streams)  # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        outs = tt.tt_apply_round_batched(W, X, 1e-6, nstreams=nstreams, streams=streams)
+        torch.cuda.synchronize(dev)
+        sec = time.perf_counter() - t0
+        flops = 0.0
+        for x, w, o in zip(X, W, outs):
+            yr = [a * b for a, b in zip(w.ranks, x.ranks)]
+            flops += apply_flops(w.ranks, x.ranks, x.dims) + round_flops(yr, o.ranks, x.dims)["total"]
+        res[form] = {"value": round(flops / sec / 1e9, 3), "unit": "GFLOP/s", "seconds": round(sec, 3),
+                     "nominal_flops": flops}
+        outs_by_form[form] = outs
+    # error of the mixed results against the oracle (inputs are the FP32 values in FP64)
+    order = sorted(range(n_tt), key=lambda i: shapes[i][0] * (shapes[i][1] * shapes[i][2]) ** 3)[:n_err]
+    errs = []
+    for i in order:
+        x64 = [c.astype(np.float32).astype(np.float64) for c in xs[i]]
+        w64 = [c.astype(np.float32).astype(np.float64) for c in ws[i]]
+        ref = ocore.round_tt(ocore.apply_mpo(w64, x64), 1e-6)
+        errs.append(ocore.rel_err(outs_by_form["mixed"][i].numpy(), ref))
+    return {"workload": f"{n_tt} trains, L~U[20,60], rank~U[8,128], MPO rank~U{{3,4,5}}, eps=1e-6, "
+                        f"{nstreams} streams (host-timed, one batch)",
+            "mixed": res["mixed"], "fp64": res["fp64"],
+            "speedup_mixed_vs_fp64": round(res["fp64"]["seconds"] / res["mixed"]["seconds"], 3),
+            "mixed_rel_err_vs_oracle_max": max(errs), "mixed_err_sample": f"{n_err} cheapest trains"}
 
 
 def bench_eval(tt, dev, n=1 << 20, L=40, r=64):
@@ -420,6 +444,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--batch-trains", type=int, default=64,
+                    help="trains in the secondary batched workload (the full batch is 512)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

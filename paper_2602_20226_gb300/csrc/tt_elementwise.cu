@@ -251,6 +251,16 @@ __global__ void f64_to_f32_kernel(const double* a, long long n, float* b) {
     b[e] = (float)a[e];
 }
 
+// G <- 1.5 I - 0.5 G  (n x n, column-major): the Newton-Schulz factor for U^T U = G
+__global__ void ns_h_kernel(float* G, int n) {
+  const long long total = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), c = (int)(e / n);
+    G[e] = (i == c ? 1.5f : 0.0f) - 0.5f * G[e];
+  }
+}
+
 inline int grid_for(long long total, int per_block, int cap = 1 << 20) {
   return (int)std::max<long long>(1, std::min<long long>(ceil_div(total, per_block), cap));
 }
@@ -348,6 +358,12 @@ int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out) {
 
 int convert_f64_to_f32(cudaStream_t s, const double* a, long long n, float* b) {
   f64_to_f32_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(a, n, b);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+int newton_schulz_h(cudaStream_t s, float* G, int n) {
+  ns_h_kernel<<<grid_for((long long)n * n, 256, 4096), 256, 0, s>>>(G, n);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }

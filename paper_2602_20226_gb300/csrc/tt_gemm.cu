@@ -24,9 +24,10 @@ namespace tt {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
-template <typename TA, typename TB, typename TC>
+// BM x BN tile, 16 x 16 threads, (BM / 16) x (BN / 16) outputs per thread.
+template <int BM, int BN, typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, double alpha,
                                                        const TA* __restrict__ A, int64_t sam,
                                                        int64_t sak, const TB* __restrict__ B,
@@ -42,11 +43,12 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  Acc acc[4][4], cmp[4][4];  // cmp: the collected rounding errors (Dot2 only)
+  constexpr int TM = BM / 16, TN = BN / 16;
+  Acc acc[TM][TN], cmp[TM][TN];  // cmp: the collected rounding errors (Dot2 only)
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = Acc(0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = cmp[i][j] = Acc(0);
 
   const bool a_m_fast = (sam == 1);
   const bool b_n_fast = (sbn == 1);
@@ -87,15 +89,15 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      Acc a[4], b[4];
+      Acc a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
           if constexpr (kDot2) {
             const float p = __fmul_rn(a[i], b[j]);
             const float e = __fmaf_rn(a[i], b[j], -p);  // a b = p + e exactly
@@ -113,11 +115,11 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       TC* p = C + (int64_t)gm * scm + (int64_t)gn * scn;
@@ -153,10 +155,21 @@ int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t
     TT_LAUNCH_CHECK();
     return TT_OK;
   }
-  dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM));
-  if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm: M too large");
-  gemm_simt_kernel<TA, TB, TC>
-      <<<grid, NT, 0, s>>>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+  // 64 x 64 tiles while they give at least one CTA per SM; 32 x 32 tiles below that, so
+  // that small products (the rank-nb updates of the QR, K = nb) still spread over the
+  // SMs: a 64 x 64 x 16 FP64 tile is ~16 us of one SM's 2 DFMA / clock.
+  const int64_t big = ceil_div(N, 64) * ceil_div(M, 64);
+  if (big >= num_sms()) {
+    dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
+    if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm: M too large");
+    gemm_simt_kernel<64, 64, TA, TB, TC>
+        <<<grid, NT, 0, s>>>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+  } else {
+    dim3 grid((unsigned)ceil_div(N, 32), (unsigned)ceil_div(M, 32));
+    if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm: M too large");
+    gemm_simt_kernel<32, 32, TA, TB, TC>
+        <<<grid, NT, 0, s>>>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+  }
   TT_LAUNCH_CHECK();
   return TT_OK;
 }

@@ -92,5 +92,6 @@ template <typename T>
 int copy_matrix(cudaStream_t s, const T* src, int p, int n, T* dst);
 
 int convert_f64_to_f32(cudaStream_t s, const double* a, long long n, float* b);
+int newton_schulz_h(cudaStream_t s, float* G, int n);  // G <- 1.5 I - 0.5 G
 
 }  // namespace tt

@@ -342,7 +342,11 @@ __global__ void init_thin_q_kernel(T* Q, int m, int p, int ldq) {
 
 constexpr size_t kPanelSmem = 180 * 1024;
 constexpr int kClusterSize = 8;       // CTAs sharing one panel
-constexpr int kClusterMinRows = 256;  // shorter panels stay on one CTA
+// Panels of at least this many rows go to the cluster kernel; shorter ones stay on one CTA.
+template <typename T>
+constexpr int cluster_min_rows() {
+  return sizeof(T) == 8 ? 256 : 256;
+}
 
 template <typename T>
 int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
@@ -365,7 +369,7 @@ int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
     const int mr = m - j0;
     const int chunk = (int)ceil_div(mr, kClusterSize);
     const size_t chunk_bytes = (size_t)chunk * jb * sizeof(T);
-    if (mr >= kClusterMinRows && chunk_bytes <= kPanelSmem) {
+    if (mr >= cluster_min_rows<T>() && chunk_bytes <= kPanelSmem) {
       // cluster panel: kClusterSize CTAs share the rows
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(kClusterSize);

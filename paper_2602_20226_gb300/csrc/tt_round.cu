@@ -52,7 +52,7 @@ Dims dims_of(const tt_train* x) {
 template <typename T>
 struct Bufs {
   T *A = nullptr, *Q = nullptr, *tmp = nullptr, *Rbuf = nullptr, *vsel = nullptr, *F = nullptr;
-  float *X32 = nullptr, *V32 = nullptr;  // mixed-form bond SVD
+  float *X32 = nullptr, *V32 = nullptr, *G32 = nullptr;  // mixed-form bond SVD
   double* W64 = nullptr;
   QrWork<T> qr;
   SvdWork sv;
@@ -76,6 +76,7 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   if (std::is_same<T, float>::value) {
     B.X32 = c.take<float>((size_t)D.r_max * D.r_max);
     B.V32 = c.take<float>((size_t)D.r_max * D.r_max);
+    B.G32 = c.take<float>((size_t)D.r_max * D.r_max);
     B.W64 = c.take<double>((size_t)D.r_max * D.r_max);
   }
   B.sv.sigma = c.take<double>(D.r_max);
@@ -86,6 +87,7 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   B.sv.status = c.take<unsigned>(1);
   B.sv.sweeps = c.take<int>(1);
   B.sv.norm = c.take<double>(1);
+  B.sv.epoch = c.take<unsigned>((size_t)D.r_max + 2);
   return c.off + 256;
 }
 
@@ -94,9 +96,8 @@ int panel_width() {
   return sizeof(T) == 8 ? 16 : 32;
 }
 
-// Column-orthogonality tolerance of the FP64 sweeps that finish a mixed-form bond SVD
-// (times sqrt(p)): far below the FP32 rounding of the cores that the factors go into.
-constexpr double kMixedRefineTol = 1.0 / (1 << 30);
+// Relative resolution of the mixed form's bond SVD (see the truncation call).
+constexpr double kMixedSigmaFloor = 1.0 / (1 << 22);
 
 template <typename T>
 double jacobi_tol(int nrow) {
@@ -307,24 +308,27 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         const bool mixed_svd = std::is_same<T, float>::value && jacobi_block_smem(p, p) <= 200 * 1024;
         if (mixed_svd) {
           // Mixed form: FP32 one-sided Jacobi with accumulated rotations V (block
-          // round-robin) does the bulk of the diagonalisation; W = X V is re-formed in
-          // FP64 and finished by FP64 one-sided Jacobi sweeps.  W's columns are already
-          // orthogonal to the FP32 tolerance, so the FP64 sweeps converge in one or two
-          // (quadratic convergence), and sigma, the truncation decision and U are FP64.
+          // round-robin), then W = X V re-formed in FP64 from the FP64 copy of the factor.
+          // W's columns are orthogonal to eta ~ sqrt(p) 2^-24, so their FP64 norms give the
+          // singular values to O(eta^2) relative accuracy (the Gram matrix of W is diagonal
+          // up to eta), and sigma and the truncation decision are FP64.  The kept left
+          // vectors W_j / sigma_j are re-orthonormalised below.
           TT_TRY(convert_f64_to_f32(s, B.sv.X, (int64_t)p * p, B.X32));
           TT_TRY(jacobi_block_f32(s, B.sv, B.X32, p, p, p, B.V32, p, 30));
           if (tm.on) TT_TRY(read_back(s, B.sv.sweeps, &sweeps32, sizeof(int)));
           TT_TRY((gemm<double, float, double>(s, p, p, p, 1.0, B.sv.X, 1, p, B.V32, 1, p, 0.0, B.W64, 1, p)));
           TT_CUDA_CHECK(cudaMemcpyAsync(B.sv.X, B.W64, (size_t)p * p * sizeof(double),
                                         cudaMemcpyDeviceToDevice, s));
-          TT_TRY(jacobi_svd(s, B.sv, p, p, kMixedRefineTol * std::sqrt((double)p), 30, delta_scale));
         } else {
           // one-sided Jacobi on the columns of the square factor X (p x p)
           TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30, delta_scale));
         }
         prof.end(pe, PROF_JACOBI, 12.0 * p * (double)p * p);
         tm.mark(5);
-        TT_TRY(svd_truncate(s, B.sv, p, p, delta_scale, max_rank));
+        // the FP32 Jacobi resolves singular values down to ~2^-24 sigma_1 plus the rounding
+        // its rotations leave in small columns; below 2^-22 sigma_1 a column is noise
+        // (nearly dependent on others), which would also defeat the Newton-Schulz step
+        TT_TRY(svd_truncate(s, B.sv, p, p, delta_scale, max_rank, mixed_svd ? kMixedSigmaFloor : 0.0));
         int rk[2] = {0, 0};
         TT_TRY(read_back(s, B.sv.rank, &rk[0], sizeof(int)));
         TT_TRY(read_back(s, B.sv.sweeps, &rk[1], sizeof(int)));
@@ -339,6 +343,15 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         // U_r (p x r') = X[:, perm[:r']] / sigma
         pe = prof.begin();
         TT_TRY(svd_left_vectors<T>(s, B.sv, p, rn, B.vsel));
+        if (mixed_svd) {
+          // one Newton-Schulz step U <- U (3I - U^T U) / 2 takes the orthogonality defect
+          // eta of the FP32 Jacobi's vectors to O(eta^2) (Dot2 GEMMs keep it accurate)
+          float* U = reinterpret_cast<float*>(B.vsel);
+          TT_TRY((gemm_core<float>(s, rn, rn, p, 1.0, U, p, 1, U, 1, p, 0.0, B.G32, 1, rn, B.sv.status)));
+          TT_TRY(newton_schulz_h(s, B.G32, rn));
+          TT_TRY((gemm_core<float>(s, p, rn, rn, 1.0, U, 1, p, B.G32, 1, rn, 0.0, B.X32, 1, p, B.sv.status)));
+          TT_CUDA_CHECK(cudaMemcpyAsync(U, B.X32, (size_t)p * rn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
         if (tall) {
           // C_k <- Q U_r (m x r', row-major);  F = U_r^T R (r' x n, row-major)
           TT_TRY((gemm_core<T>(s, m, rn, p, 1.0, B.Q, 1, m, B.vsel, 1, p, 0.0, slot[k], rn, 1, B.sv.status)));

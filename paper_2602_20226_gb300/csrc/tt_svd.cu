@@ -90,11 +90,43 @@ __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __r
   return true;
 }
 
-template <int NT, int TPL>
+// Epoch handshake of the dataflow ordering: column c has been through epoch[c] rounds.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Lane 0 waits (bounded) until column c has finished round t-1, i.e. epoch[c] >= t.
+__device__ __forceinline__ bool wait_column(const unsigned* epoch, int c, unsigned t, unsigned* status) {
+  long long polls = 0;
+  while (ld_acquire_u32(epoch + c) < t) {
+    if (++polls > (1ll << 24)) {
+      atomicOr(status, (unsigned)ST_TIMEOUT);
+      return false;
+    }
+    if ((polls & 255) == 0 && (*(volatile unsigned*)status & ST_TIMEOUT)) return false;
+  }
+  return true;
+}
+
+// FLOW = false: a grid barrier after every round (p - 1 per sweep).
+// FLOW = true (dataflow ordering): each column carries an epoch counter; the warp that
+// takes pair (a, b) in round t waits only until both columns have left round t - 1 (an
+// acquire load of their counters), rotates them and releases both counters to t + 1.
+// In the round-robin ordering every column is in exactly one pair per round, so the
+// dependencies of a pair are the two pairs that last held its columns; warps run ahead
+// as far as their inputs allow and a grid barrier is needed only once per sweep, for
+// the convergence test.  All CTAs are co-resident (cooperative launch) and every warp
+// takes its rounds in order, so the waits cannot form a cycle; each wait is bounded.
+template <int NT, int TPL, bool FLOW>
 __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int ncol, int ldx,
                                                     double tol, double negl_scale, const double* norm,
                                                     int max_sweeps, unsigned* bar, unsigned* rot,
-                                                    unsigned* status, int* sweeps_out) {
+                                                    unsigned* status, int* sweeps_out, unsigned* epoch) {
   constexpr int WPB = NT / 32;
   const double nl = negl_scale > 0.0 ? negl_scale * __ldcg(norm) : 0.0;
   const double negl = nl * nl;
@@ -106,9 +138,11 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
 
   int sweep = 0;
   bool converged = false;
+  bool ok = true;
+  unsigned t = 0;  // rounds completed before the current one (dataflow epoch)
   for (; sweep < max_sweeps && !converged; ++sweep) {
-    for (int rnd = 0; rnd < N - 1; ++rnd) {
-      for (int q = gw; q < npairs; q += GW) {
+    for (int rnd = 0; rnd < N - 1; ++rnd, ++t) {
+      for (int q = gw; ok && q < npairs; q += GW) {
         int a, b;
         if (q == 0) {
           a = rnd;
@@ -117,18 +151,37 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
           a = (rnd + q) % (N - 1);
           b = (rnd - q + N - 1) % (N - 1);
         }
-        if (a >= ncol || b >= ncol) continue;
         if (a > b) {
-          const int t = a;
+          const int tmp = a;
           a = b;
-          b = t;
+          b = tmp;
         }
-        if (rotate_pair<TPL>(X + (int64_t)a * ldx, X + (int64_t)b * ldx, nrow, lane, tol, negl) &&
+        // a < b, so only b can be the padding column N - 1 (odd ncol)
+        const bool real_b = b < ncol;
+        if (FLOW) {
+          int good = 1;
+          if (lane == 0) good = wait_column(epoch, a, t, status) && (!real_b || wait_column(epoch, b, t, status));
+          good = __shfl_sync(0xffffffffu, good, 0);
+          if (!good) {
+            ok = false;
+            break;
+          }
+        }
+        if (real_b && rotate_pair<TPL>(X + (int64_t)a * ldx, X + (int64_t)b * ldx, nrow, lane, tol, negl) &&
             lane == 0)
           atomicAdd(rot + sweep, 1u);
+        if (FLOW) {
+          __syncwarp();
+          if (lane == 0) {
+            __threadfence();
+            st_release_u32(epoch + a, t + 1);
+            if (real_b) st_release_u32(epoch + b, t + 1);
+          }
+        }
       }
-      if (!sweep_barrier(bar, status)) return;
+      if (!FLOW && !sweep_barrier(bar, status)) return;
     }
+    if (FLOW && !sweep_barrier(bar, status)) return;  // also ends a CTA whose wait expired
     converged = (*(volatile unsigned*)(rot + sweep) == 0u);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -144,26 +197,138 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
 // inner rounds), then writes them back.  Group pairs follow the round-robin order,
 // so a grid barrier is needed only between outer rounds: 2G - 1 per sweep for G
 // groups instead of p - 1.  The mixed form uses it as the fast part of its bond SVD.
-constexpr int kJbGroup = 16;
+// Global -> shared copy of the C2 columns listed in cols (n values each, column c of
+// src at src + cols[c] * ld; -1 = zero column), U independent loads in flight per
+// thread so the copy costs a few L2 latencies, not one per element.
+template <int U>
+__device__ __forceinline__ void load_cols(float* __restrict__ dst, const float* __restrict__ src,
+                                          const int* cols, int C2, int n, int ld) {
+  const int total = C2 * n;
+  for (int base = threadIdx.x; base < total; base += blockDim.x * U) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      v[u] = 0.f;
+      if (e < total) {
+        const int c = e / n;
+        if (cols[c] >= 0) v[u] = __ldcg(src + (e - c * n) + (int64_t)cols[c] * ld);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < total) dst[e] = v[u];
+    }
+  }
+}
 
-__global__ void __launch_bounds__(512) jacobi_block_f32_kernel(float* X, int nrow, int ncol, int ldx,
-                                                                float* V, int ldv, float tol,
-                                                                int max_sweeps, unsigned* bar,
-                                                                unsigned* rot, unsigned* status,
-                                                                int* sweeps_out) {
+__device__ __forceinline__ void store_cols(const float* __restrict__ srcs, float* __restrict__ dst,
+                                           const int* cols, int C2, int n, int ld) {
+  const int total = C2 * n;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int c = e / n;
+    if (cols[c] >= 0) __stcg(dst + (e - c * n) + (int64_t)cols[c] * ld, srcs[e]);
+  }
+}
+
+// One FP32 Jacobi rotation of the shared-memory columns (xa, xb) of length nrow, applied
+// to (va, vb) of length ncol as well; the columns are read in chunks of 32 * TPL values
+// held in registers (one chunk: read once, rotated from registers).
+template <int TPL>
+__device__ __forceinline__ bool rotate_pair_f32(float* xa, float* xb, float* va, float* vb, int nrow,
+                                                int ncol, int lane, float tol) {
+  constexpr int CH = 32 * TPL;
+  float ra[TPL], rb[TPL];
+  float al = 0.f, be = 0.f, ga = 0.f;
+  for (int i0 = 0; i0 < nrow; i0 += CH) {
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = i0 + lane + 32 * t;
+      ra[t] = i < nrow ? xa[i] : 0.f;
+      rb[t] = i < nrow ? xb[i] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      al = fmaf(ra[t], ra[t], al);
+      be = fmaf(rb[t], rb[t], be);
+      ga = fmaf(ra[t], rb[t], ga);
+    }
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (!(ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
+  const float zeta = (be - al) / (2.f * ga);
+  const float tn = (fabsf(zeta) > 1e18f) ? 0.5f / zeta
+                                         : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = 1.f / sqrtf(1.f + tn * tn);
+  const float s = c * tn;
+  if (s == 0.f) return false;
+  for (int i0 = 0; i0 < nrow; i0 += CH) {
+    if (nrow > CH) {  // several chunks: the registers hold the last one, reload
+#pragma unroll
+      for (int t = 0; t < TPL; ++t) {
+        const int i = i0 + lane + 32 * t;
+        ra[t] = i < nrow ? xa[i] : 0.f;
+        rb[t] = i < nrow ? xb[i] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = i0 + lane + 32 * t;
+      if (i < nrow) {
+        xa[i] = c * ra[t] - s * rb[t];
+        xb[i] = s * ra[t] + c * rb[t];
+      }
+    }
+  }
+  for (int i0 = 0; i0 < ncol; i0 += CH) {
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = i0 + lane + 32 * t;
+      ra[t] = i < ncol ? va[i] : 0.f;
+      rb[t] = i < ncol ? vb[i] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = i0 + lane + 32 * t;
+      if (i < ncol) {
+        va[i] = c * ra[t] - s * rb[t];
+        vb[i] = s * ra[t] + c * rb[t];
+      }
+    }
+  }
+  return true;
+}
+
+// GS columns per group, one warp per pair of the 2 GS columns in shared memory.
+// With gepoch (one counter per group) the outer rounds follow the same dataflow rule as
+// jacobi_kernel: a CTA waits only for its two groups to leave the previous outer round,
+// and the grid barrier runs once per sweep.
+template <int GS, int TPL>
+__global__ void __launch_bounds__(32 * GS) jacobi_block_f32_kernel(float* X, int nrow, int ncol, int ldx,
+                                                                   float* V, int ldv, float tol,
+                                                                   int max_sweeps, unsigned* bar,
+                                                                   unsigned* rot, unsigned* status,
+                                                                   int* sweeps_out, unsigned* gepoch) {
+  constexpr int kJbGroup = GS;
   extern __shared__ float jsm[];
   constexpr int C2 = 2 * kJbGroup;
   float* Xs = jsm;                           // C2 columns x nrow
   float* Vs = jsm + (size_t)C2 * nrow;       // C2 columns x ncol
   __shared__ int cols[C2];
   __shared__ unsigned s_rot;
+  __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = (ncol + kJbGroup - 1) / kJbGroup;
   const int NG = G + (G & 1);
+  const bool flow = gepoch != nullptr;
   int sweep = 0;
   bool converged = false;
+  unsigned t = 0;  // outer rounds completed before the current one
   for (; sweep < max_sweeps && !converged; ++sweep) {
-    for (int r = 0; r < NG - 1; ++r) {
+    for (int r = 0; r < NG - 1; ++r, ++t) {
       for (int q = blockIdx.x; q < NG / 2; q += gridDim.x) {
         int ga, gb;
         if (q == 0) {
@@ -173,6 +338,12 @@ __global__ void __launch_bounds__(512) jacobi_block_f32_kernel(float* X, int nro
           ga = (r + q) % (NG - 1);
           gb = (r - q + NG - 1) % (NG - 1);
         }
+        if (flow) {
+          if (tid == 0)
+            s_ok = (ga >= G || wait_column(gepoch, ga, t, status)) && (gb >= G || wait_column(gepoch, gb, t, status));
+          __syncthreads();
+          if (!s_ok) break;  // a wait expired: leave through the sweep barrier
+        }
         if (tid < C2) {
           const int g = tid < kJbGroup ? ga : gb;
           const int c = g * kJbGroup + (tid % kJbGroup);
@@ -180,16 +351,10 @@ __global__ void __launch_bounds__(512) jacobi_block_f32_kernel(float* X, int nro
         }
         if (tid == 0) s_rot = 0;
         __syncthreads();
-        for (int e = tid; e < C2 * nrow; e += blockDim.x) {
-          const int c = e / nrow, i = e % nrow;
-          Xs[e] = cols[c] >= 0 ? __ldcg(X + i + (int64_t)cols[c] * ldx) : 0.f;
-        }
-        for (int e = tid; e < C2 * ncol; e += blockDim.x) {
-          const int c = e / ncol, i = e % ncol;
-          Vs[e] = cols[c] >= 0 ? __ldcg(V + i + (int64_t)cols[c] * ldv) : 0.f;
-        }
+        load_cols<8>(Xs, X, cols, C2, nrow, ldx);
+        load_cols<8>(Vs, V, cols, C2, ncol, ldv);
         __syncthreads();
-        // inner round-robin over the 32 local slots: 31 rounds x 16 pairs
+        // inner round-robin over the 2 GS local slots: 2 GS - 1 rounds x GS pairs
         unsigned local = 0;
         for (int ir = 0; ir < C2 - 1; ++ir) {
           int a, b;
@@ -200,58 +365,27 @@ __global__ void __launch_bounds__(512) jacobi_block_f32_kernel(float* X, int nro
             a = (ir + warp) % (C2 - 1);
             b = (ir - warp + C2 - 1) % (C2 - 1);
           }
-          if (cols[a] >= 0 && cols[b] >= 0) {
-            float* xa = Xs + (size_t)a * nrow;
-            float* xb = Xs + (size_t)b * nrow;
-            float al = 0.f, be = 0.f, ga = 0.f;
-            for (int i = lane; i < nrow; i += 32) {
-              const float u = xa[i], v = xb[i];
-              al = fmaf(u, u, al);
-              be = fmaf(v, v, be);
-              ga = fmaf(u, v, ga);
-            }
-            al = warp_sum(al);
-            be = warp_sum(be);
-            ga = warp_sum(ga);
-            if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
-              const float zeta = (be - al) / (2.f * ga);
-              const float t = (fabsf(zeta) > 1e18f) ? 0.5f / zeta
-                                                    : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-              const float c = 1.f / sqrtf(1.f + t * t);
-              const float s = c * t;
-              if (s != 0.f) {
-                for (int i = lane; i < nrow; i += 32) {
-                  const float u = xa[i], v = xb[i];
-                  xa[i] = c * u - s * v;
-                  xb[i] = s * u + c * v;
-                }
-                float* va = Vs + (size_t)a * ncol;
-                float* vb = Vs + (size_t)b * ncol;
-                for (int i = lane; i < ncol; i += 32) {
-                  const float u = va[i], v = vb[i];
-                  va[i] = c * u - s * v;
-                  vb[i] = s * u + c * v;
-                }
-                ++local;
-              }
-            }
-          }
+          if (cols[a] >= 0 && cols[b] >= 0 &&
+              rotate_pair_f32<TPL>(Xs + (size_t)a * nrow, Xs + (size_t)b * nrow, Vs + (size_t)a * ncol,
+                                   Vs + (size_t)b * ncol, nrow, ncol, lane, tol))
+            ++local;
           __syncthreads();
         }
         if (lane == 0 && local) atomicAdd(&s_rot, local);
-        for (int e = tid; e < C2 * nrow; e += blockDim.x) {
-          const int c = e / nrow, i = e % nrow;
-          if (cols[c] >= 0) __stcg(X + i + (int64_t)cols[c] * ldx, Xs[e]);
-        }
-        for (int e = tid; e < C2 * ncol; e += blockDim.x) {
-          const int c = e / ncol, i = e % ncol;
-          if (cols[c] >= 0) __stcg(V + i + (int64_t)cols[c] * ldv, Vs[e]);
-        }
+        store_cols(Xs, X, cols, C2, nrow, ldx);
+        store_cols(Vs, V, cols, C2, ncol, ldv);
         __syncthreads();
         if (tid == 0 && s_rot) atomicAdd(rot + sweep, s_rot);
+        if (flow && tid == 0) {
+          __threadfence();
+          if (ga < G) st_release_u32(gepoch + ga, t + 1);
+          if (gb < G) st_release_u32(gepoch + gb, t + 1);
+        }
       }
-      if (!sweep_barrier(bar, status)) return;
+      if (flow && (*(volatile unsigned*)status & ST_TIMEOUT)) break;
+      if (!flow && !sweep_barrier(bar, status)) return;
     }
+    if (flow && !sweep_barrier(bar, status)) return;
     converged = (*(volatile unsigned*)(rot + sweep) == 0u);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -274,7 +408,8 @@ __global__ void identity_f32_kernel(float* V, int n, int ldv) {
 // the smallest singular value upwards, then capped at max_rank.
 __global__ void __launch_bounds__(1024) svd_truncate_kernel(
     const double* X, int nrow, int ncol, int ldx, const double* norm, double delta_scale,
-    long long max_rank, double* sig_sorted, int* perm, int* rank_out, unsigned* status) {
+    long long max_rank, double rel_floor, double* sig_sorted, int* perm, int* rank_out,
+    unsigned* status) {
   extern __shared__ double sh[];
   double* sig = sh;
   double* srt = sh + ncol;
@@ -320,6 +455,9 @@ __global__ void __launch_bounds__(1024) svd_truncate_kernel(
     for (int j = 0; j < ncol; ++j) finite = finite && isfinite(srt[j]);
     if (!finite) atomicOr(status, (unsigned)ST_NONFINITE);
     if (r > nrow) r = nrow;  // R has rank <= its row count
+    // singular values below the resolution of the arithmetic that produced the factor
+    // (rel_floor * sigma_1) are not kept, whatever delta allows
+    while (r > 1 && srt[r - 1] < rel_floor * srt[0]) --r;
     if (r < 1) r = 1;
     if (max_rank > 0 && r > max_rank) r = (int)max_rank;
     *rank_out = r;
@@ -401,30 +539,34 @@ int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, do
                   int max_sweeps) {
   const int npairs = (ncol + 1) / 2;
   if (ncol <= 48) {
-    jacobi_kernel<256, TPL><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, negl_scale, w.norm, max_sweeps,
-                                               w.bar, w.rot, w.status, w.sweeps);
+    jacobi_kernel<256, TPL, false><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, negl_scale, w.norm,
+                                                      max_sweeps, w.bar, w.rot, w.status, w.sweeps, nullptr);
     TT_LAUNCH_CHECK();
     return TT_OK;
   }
+  // the dataflow ordering needs one epoch counter per column (SvdWork::epoch)
+  const bool flow = w.epoch != nullptr;
+  const void* fn = flow ? (const void*)jacobi_kernel<NT, TPL, true> : (const void*)jacobi_kernel<NT, TPL, false>;
   static int cfg_dev = -1, cfg_blocks = 0;
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (cfg_dev != dev) {
-    int occ = 0;
-    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel<NT, TPL>, NT, 0));
-    cfg_blocks = occ * num_sms();
+    int occ_a = 0, occ_b = 0;
+    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, jacobi_kernel<NT, TPL, true>, NT, 0));
+    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, jacobi_kernel<NT, TPL, false>, NT, 0));
+    cfg_blocks = std::min(occ_a, occ_b) * num_sms();
     cfg_dev = dev;
   }
   int blocks = (int)std::min<int64_t>(ceil_div(npairs, NT / 32), cfg_blocks);
   if (blocks < 1) blocks = 1;
+  if (flow) TT_CUDA_CHECK(cudaMemsetAsync(w.epoch, 0, (size_t)ncol * sizeof(unsigned), s));
   double* X = w.X;
   int ldx = w.ldx;
   const double* nrm = w.norm;
-  unsigned *bar = w.bar, *rot = w.rot, *st = w.status;
+  unsigned *bar = w.bar, *rot = w.rot, *st = w.status, *ep = w.epoch;
   int* sw = w.sweeps;
-  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &negl_scale, &nrm, &max_sweeps, &bar, &rot, &st, &sw};
-  TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_kernel<NT, TPL>, dim3(blocks), dim3(NT),
-                                            args, 0, s));
+  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &negl_scale, &nrm, &max_sweeps, &bar, &rot, &st, &sw, &ep};
+  TT_CUDA_CHECK(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(NT), args, 0, s));
   note_launch();
   return TT_OK;
 }
@@ -446,7 +588,7 @@ int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int m
 }
 
 int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
-                 int64_t max_rank) {
+                 int64_t max_rank, double rel_floor) {
   const size_t smem = 2 * (size_t)ncol * sizeof(double);
   if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "svd_truncate: bond rank too large");
   static int configured_dev = -1;
@@ -458,7 +600,8 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
     configured_dev = dev;
   }
   svd_truncate_kernel<<<1, 1024, smem, s>>>(w.X, nrow, ncol, w.ldx, w.norm, delta_scale,
-                                            (long long)max_rank, w.sigma, w.perm, w.rank, w.status);
+                                            (long long)max_rank, rel_floor, w.sigma, w.perm, w.rank,
+                                            w.status);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }
@@ -482,24 +625,27 @@ int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ld
   return TT_OK;
 }
 
-size_t jacobi_block_smem(int nrow, int ncol) {
-  return (size_t)2 * kJbGroup * ((size_t)nrow + ncol) * sizeof(float);
+size_t jacobi_block_smem_gs(int gs, int nrow, int ncol) {
+  return (size_t)2 * gs * ((size_t)nrow + ncol) * sizeof(float);
 }
 
-int jacobi_block_f32(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, int ldx, float* V, int ldv,
-                     int max_sweeps) {
-  if (ncol <= 0 || nrow <= 0) return TT_OK;
-  const size_t smem = jacobi_block_smem(nrow, ncol);
-  if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "jacobi_block_f32: factor too large");
-  if (max_sweeps > SvdWork::kMaxSweeps) max_sweeps = SvdWork::kMaxSweeps;
+size_t jacobi_block_smem(int nrow, int ncol) { return jacobi_block_smem_gs(16, nrow, ncol); }
+
+namespace {
+
+template <int GS, int TPL>
+int launch_jacobi_block(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, int ldx, float* V,
+                        int ldv, int max_sweeps) {
+  constexpr int NT = 32 * GS;
+  const size_t smem = jacobi_block_smem_gs(GS, nrow, ncol);
   static int cfg_dev = -1, cfg_blocks = 0;
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (cfg_dev != dev) {
-    TT_CUDA_CHECK(cudaFuncSetAttribute(jacobi_block_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TT_CUDA_CHECK(cudaFuncSetAttribute(jacobi_block_f32_kernel<GS, TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
     int occ = 0;
-    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_block_f32_kernel, 512,
+    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_block_f32_kernel<GS, TPL>, NT,
                                                                 200 * 1024));
     cfg_blocks = std::max(1, occ) * num_sms();
     cfg_dev = dev;
@@ -509,18 +655,36 @@ int jacobi_block_f32(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, i
   TT_LAUNCH_CHECK();
   TT_CUDA_CHECK(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
   TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
-  const int G = (ncol + kJbGroup - 1) / kJbGroup;
+  const int G = (ncol + GS - 1) / GS;
   const int NG = G + (G & 1);
   int blocks = std::min(NG / 2, cfg_blocks);
   if (blocks < 1) blocks = 1;
   const float tol = std::sqrt((float)std::max(nrow, 1)) * 5.9604645e-8f;
   unsigned *bar = w.bar, *rot = w.rot, *st = w.status;
   int* sw = w.sweeps;
-  void* args[] = {&X, &nrow, &ncol, &ldx, &V, &ldv, (void*)&tol, &max_sweeps, &bar, &rot, &st, &sw};
-  TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_block_f32_kernel, dim3(blocks), dim3(512),
+  unsigned* ep = w.epoch;
+  if (ep) TT_CUDA_CHECK(cudaMemsetAsync(ep, 0, (size_t)G * sizeof(unsigned), s));
+  void* args[] = {&X, &nrow, &ncol, &ldx, &V, &ldv, (void*)&tol, &max_sweeps, &bar, &rot, &st, &sw, &ep};
+  TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_block_f32_kernel<GS, TPL>, dim3(blocks), dim3(NT),
                                             args, smem, s));
   note_launch();
   return TT_OK;
+}
+
+}  // namespace
+
+int jacobi_block_f32(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, int ldx, float* V, int ldv,
+                     int max_sweeps) {
+  if (ncol <= 0 || nrow <= 0) return TT_OK;
+  if (max_sweeps > SvdWork::kMaxSweeps) max_sweeps = SvdWork::kMaxSweeps;
+  // group size GS: p / (2 GS) CTAs share the work of an outer round
+  constexpr int kGroup = 16;
+  if (jacobi_block_smem_gs(kGroup, nrow, ncol) > 200 * 1024)
+    return fail(TT_ERR_UNSUPPORTED, "jacobi_block_f32: factor too large");
+  const int len = std::max(nrow, ncol);  // register chunk: 32 * TPL values per column
+  if (len <= 128) return launch_jacobi_block<kGroup, 4>(s, w, X, nrow, ncol, ldx, V, ldv, max_sweeps);
+  if (len <= 256) return launch_jacobi_block<kGroup, 8>(s, w, X, nrow, ncol, ldx, V, ldv, max_sweeps);
+  return launch_jacobi_block<kGroup, 12>(s, w, X, nrow, ncol, ldx, V, ldv, max_sweeps);
 }
 
 template <typename TO>

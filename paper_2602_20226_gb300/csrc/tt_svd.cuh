@@ -17,6 +17,7 @@ struct SvdWork {
   unsigned* status = nullptr;
   int* sweeps = nullptr;
   double* norm = nullptr;   // device double ||x||
+  unsigned* epoch = nullptr;  // [p] per-column round counters (dataflow Jacobi); null: barrier per round
 };
 
 // One-sided Jacobi on the columns of X (nrow x ncol); the rotations are not kept.
@@ -31,9 +32,10 @@ size_t jacobi_block_smem(int nrow, int ncol);
 int jacobi_block_f32(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, int ldx, float* V, int ldv,
                      int max_sweeps);
 
-// sigma, perm and the truncation rank with delta = delta_scale * (*norm).
+// sigma, perm and the truncation rank with delta = delta_scale * (*norm); singular values
+// below rel_floor * sigma_1 are dropped as well (0 in the FP64 form).
 int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_scale,
-                 int64_t max_rank);
+                 int64_t max_rank, double rel_floor = 0.0);
 
 // No-truncation certificate for the upper-triangular p x p factor R (FP64, ld ldr):
 // *w.rank <- 1 if sigma_min(R) > delta = delta_scale * (*w.norm) is proven, else 0;

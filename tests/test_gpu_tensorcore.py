@@ -132,3 +132,20 @@ def test_mixed_round_ragged(cuda_lib, case):
     ref = core.round_tt(x, 1e-6)
     got, _ = _mixed_round(tt, x, 1e-6)
     assert core.rel_err(got, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("case", ["laplacian", "hadamard"])
+@pytest.mark.parametrize("eps", [1e-8, 1e-10])
+def test_mixed_round_below_fp32_resolution(cuda_lib, case, eps):
+    """eps below what FP32 factors resolve: the mixed form drops the noise-level singular
+    values (< 2^-22 sigma_1 at each bond) and stays within a few 1e-7 of the train."""
+    if case == "laplacian":
+        x = _f32(inputs.random_tt(5, 20, 2, 32))
+        y = _f32(core.apply_mpo(structured.laplacian_mpo(2, 10), x))
+    else:
+        h = inputs.random_tt(12, 14, 2, 6)
+        y = _f32(core.hadamard(h, h))
+    got, nrm = _mixed_round(cuda_lib, y, eps)
+    assert all(np.isfinite(c).all() for c in got)
+    assert core.rel_err(got, y) <= 2e-6
+    assert abs(nrm - core.norm(y)) <= 1e-6 * core.norm(y)
