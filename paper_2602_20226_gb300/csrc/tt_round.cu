@@ -246,7 +246,7 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
   TT_TRY(frobenius_norm<T>(s, slot[0], cur[0] * d[0] * cur[1], B.sv.norm));
 
   // ---- 2. left-to-right truncated SVD sweep
-  int total_sweeps = 0, certified_bonds = 0;
+  int total_sweeps = 0, certified_bonds = 0, refined_bonds = 0;
   if (L > 1) {
     const double delta_scale = eps / std::sqrt((double)(L - 1));
     for (int k = 0; k < L - 1; ++k) {
@@ -315,10 +315,16 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
           // vectors W_j / sigma_j are re-orthonormalised below.
           TT_TRY(convert_f64_to_f32(s, B.sv.X, (int64_t)p * p, B.X32));
           TT_TRY(jacobi_block_f32(s, B.sv, B.X32, p, p, p, B.V32, p, 30));
-          if (tm.on) TT_TRY(read_back(s, B.sv.sweeps, &sweeps32, sizeof(int)));
           TT_TRY((gemm<double, float, double>(s, p, p, p, 1.0, B.sv.X, 1, p, B.V32, 1, p, 0.0, B.W64, 1, p)));
           TT_CUDA_CHECK(cudaMemcpyAsync(B.sv.X, B.W64, (size_t)p * p * sizeof(double),
                                         cudaMemcpyDeviceToDevice, s));
+          TT_TRY(read_back(s, B.sv.sweeps, &sweeps32, sizeof(int)));
+          if (sweeps32 < 0) {
+            // the FP32 sweeps did not settle: finish the (nearly diagonalised) W = X V with
+            // FP64 one-sided Jacobi, which converges from there in a few sweeps
+            TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<double>(p), 30, delta_scale));
+            ++refined_bonds;
+          }
         } else {
           // one-sided Jacobi on the columns of the square factor X (p x p)
           TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30, delta_scale));
@@ -383,8 +389,10 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
   if (norm_out) *norm_out = nrm;
   if (stats) stats->jacobi_sweeps = total_sweeps;
   if (tm.on)
-    std::fprintf(stderr, "[tt_round trace] jacobi sweeps total=%d, bonds certified full rank=%d\n",
-                 total_sweeps, certified_bonds);
+    std::fprintf(stderr,
+                 "[tt_round trace] jacobi sweeps total=%d, bonds certified full rank=%d, "
+                 "FP32 Jacobi finished in FP64=%d\n",
+                 total_sweeps, certified_bonds, refined_bonds);
   if (!std::isfinite(nrm) || (st & ST_NONFINITE)) return fail(TT_ERR_NUMERIC, "tt_round: non-finite values");
   if (st & ST_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_round: device wait expired");
   if (st & ST_NONCONVERGED) return fail(TT_ERR_NUMERIC, "tt_round: Jacobi SVD hit its sweep cap");

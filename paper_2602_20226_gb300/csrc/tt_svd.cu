@@ -237,7 +237,7 @@ __device__ __forceinline__ void store_cols(const float* __restrict__ srcs, float
 // held in registers (one chunk: read once, rotated from registers).
 template <int TPL>
 __device__ __forceinline__ bool rotate_pair_f32(float* xa, float* xb, float* va, float* vb, int nrow,
-                                                int ncol, int lane, float tol) {
+                                                int ncol, int lane, float tol, float negl) {
   constexpr int CH = 32 * TPL;
   float ra[TPL], rb[TPL];
   float al = 0.f, be = 0.f, ga = 0.f;
@@ -258,6 +258,7 @@ __device__ __forceinline__ bool rotate_pair_f32(float* xa, float* xb, float* va,
   al = warp_sum(al);
   be = warp_sum(be);
   ga = warp_sum(ga);
+  if (al < negl && be < negl) return false;  // two noise-level columns: both are dropped
   if (!(ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
   const float zeta = (be - al) / (2.f * ga);
   const float tn = (fabsf(zeta) > 1e18f) ? 0.5f / zeta
@@ -311,8 +312,11 @@ __global__ void __launch_bounds__(32 * GS) jacobi_block_f32_kernel(float* X, int
                                                                    float* V, int ldv, float tol,
                                                                    int max_sweeps, unsigned* bar,
                                                                    unsigned* rot, unsigned* status,
-                                                                   int* sweeps_out, unsigned* gepoch) {
+                                                                   int* sweeps_out, unsigned* gepoch,
+                                                                   float negl_scale, const double* norm) {
   constexpr int kJbGroup = GS;
+  const float nl = negl_scale > 0.f ? negl_scale * (float)__ldcg(norm) : 0.f;
+  const float negl = nl * nl;
   extern __shared__ float jsm[];
   constexpr int C2 = 2 * kJbGroup;
   float* Xs = jsm;                           // C2 columns x nrow
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(32 * GS) jacobi_block_f32_kernel(float* X, int
           }
           if (cols[a] >= 0 && cols[b] >= 0 &&
               rotate_pair_f32<TPL>(Xs + (size_t)a * nrow, Xs + (size_t)b * nrow, Vs + (size_t)a * ncol,
-                                   Vs + (size_t)b * ncol, nrow, ncol, lane, tol))
+                                   Vs + (size_t)b * ncol, nrow, ncol, lane, tol, negl))
             ++local;
           __syncthreads();
         }
@@ -388,10 +392,8 @@ __global__ void __launch_bounds__(32 * GS) jacobi_block_f32_kernel(float* X, int
     if (flow && !sweep_barrier(bar, status)) return;
     converged = (*(volatile unsigned*)(rot + sweep) == 0u);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *sweeps_out = sweep;
-    if (!converged) atomicOr(status, (unsigned)ST_NONCONVERGED);
-  }
+  // the caller decides what a cap means here: -1 reports it (no status flag)
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = converged ? sweep : -1;
 }
 
 __global__ void identity_f32_kernel(float* V, int n, int ldv) {
@@ -659,12 +661,21 @@ int launch_jacobi_block(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol
   const int NG = G + (G & 1);
   int blocks = std::min(NG / 2, cfg_blocks);
   if (blocks < 1) blocks = 1;
-  const float tol = std::sqrt((float)std::max(nrow, 1)) * 5.9604645e-8f;
+  // 8 sqrt(n) 2^-24: the rounding of an FP32 dot product of n terms is ~sqrt(n) 2^-24
+  // of |a| |b|, so a smaller tolerance can keep rotating on noise (it did for n = 2); the
+  // kept vectors are re-orthonormalised afterwards, which absorbs this defect
+  const float tol = 8.f * std::sqrt((float)std::max(nrow, 1)) * 5.9604645e-8f;
   unsigned *bar = w.bar, *rot = w.rot, *st = w.status;
   int* sw = w.sweeps;
   unsigned* ep = w.epoch;
   if (ep) TT_CUDA_CHECK(cudaMemsetAsync(ep, 0, (size_t)G * sizeof(unsigned), s));
-  void* args[] = {&X, &nrow, &ncol, &ldx, &V, &ldv, (void*)&tol, &max_sweeps, &bar, &rot, &st, &sw, &ep};
+  // pairs of columns below 2^-22 ||x|| / sqrt(2 p) are left alone: that is under the
+  // mixed form's resolution floor (2^-22 sigma_1 >= 2^-22 ||x|| / sqrt(p)), FP32
+  // rotations cannot make such noise columns orthogonal, and the truncation drops them
+  float negl_scale = (float)(1.0 / (1 << 22) / std::sqrt(2.0 * std::max(ncol, 1)));
+  const double* nrm = w.norm;
+  void* args[] = {&X, &nrow, &ncol, &ldx, &V, &ldv, (void*)&tol, &max_sweeps, &bar, &rot, &st, &sw, &ep,
+                  &negl_scale, &nrm};
   TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_block_f32_kernel<GS, TPL>, dim3(blocks), dim3(NT),
                                             args, smem, s));
   note_launch();

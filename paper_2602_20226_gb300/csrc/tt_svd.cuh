@@ -27,7 +27,9 @@ int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int m
                double delta_scale = 0.0);
 
 // FP32 one-sided Jacobi with accumulated rotations (V = I on entry is set here), block
-// round-robin in shared memory; the fast part of the mixed form's bond SVD.
+// round-robin in shared memory; the fast part of the mixed form's bond SVD.  *w.sweeps
+// receives the sweep count, or -1 if max_sweeps passed without convergence (no status
+// flag is raised: the caller finishes the SVD in FP64 then).
 size_t jacobi_block_smem(int nrow, int ncol);
 int jacobi_block_f32(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol, int ldx, float* V, int ldv,
                      int max_sweeps);

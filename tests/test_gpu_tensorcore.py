@@ -149,3 +149,17 @@ def test_mixed_round_below_fp32_resolution(cuda_lib, case, eps):
     assert all(np.isfinite(c).all() for c in got)
     assert core.rel_err(got, y) <= 2e-6
     assert abs(nrm - core.norm(y)) <= 1e-6 * core.norm(y)
+
+
+def test_mixed_round_noise_level_columns(cuda_lib):
+    """A train of the uneven batch (L = 42, r = 41, random MPO of rank 4) whose bond factors
+    carry many singular values at FP32 noise level: the FP32 Jacobi must leave pairs of such
+    columns alone (they never become orthogonal in FP32) instead of running into its cap."""
+    tt = cuda_lib
+    x = _f32(inputs.random_tt(4469, 42, 2, 41))
+    w = _f32(inputs.random_mpo(4969, 42, 2, 4))
+    y = _f32(core.apply_mpo(w, x))
+    got, nrm = _mixed_round(tt, y, 1e-6)
+    ref = core.round_tt(y, 1e-6)
+    assert all(np.isfinite(c).all() for c in got)
+    assert core.rel_err(got, ref) <= 4e-6
