@@ -132,20 +132,27 @@ int tt_round(const tt_train* x, double eps, int64_t max_rank, int32_t prec, tt_t
 
 /* ---- batched apply + round over many independent trains ---- */
 
-/* Device workspace (bytes) for tt_apply_round_batched with `nstreams` streams. */
+/* Device workspace (bytes) for tt_apply_round_batched: one rounding workspace per train
+ * (sized for its apply output) plus the job arrays of the lock-step driver.  nstreams is
+ * accepted for compatibility and does not change the size.  0 on invalid input. */
 size_t tt_apply_round_batched_workspace_size(int32_t n, const tt_mpo* W, const tt_train* x,
                                              int32_t prec, int32_t nstreams);
 
 /* For i < n: y[i] = W[i] x[i] (tt_apply_mpo), then out[i] = round(y[i], eps, max_rank)
- * (tt_round in form prec).  Trains may differ in length, modes and ranks.  The
- * library's scheduler runs nstreams host worker threads, each on one caller stream
- * and one workspace slice, taking trains largest-first (by nominal rounding work)
- * from a shared queue, so that many latency-bound sweeps run at once.
+ * (the rounding of tt_round in form prec; the same truncation rule per train, with
+ * eps ||y[i]|| / sqrt(L_i - 1)).  Trains may differ in length, modes and ranks; all
+ * must have the dtype of prec (TT_F64 / TT_PREC_FP64, TT_F32 / TT_PREC_MIXED).
+ * The trains advance in lock-step: each step of the two sweeps is one launch per
+ * operation over all trains that have that step (one job per train, own sizes), and
+ * the host synchronises once per step for the truncation ranks.  The work runs on
+ * streams[0]; streams[1..4] (when given) run the size classes of a step's bond SVDs side
+ * by side (event fork / join on streams[0]).  The job descriptors are staged in one
+ * pinned host buffer per process (allocated on first use, kept for reuse).
  *   y, out   caller-allocated outputs (y[i] sized for ranks a_k r_k; out[i] like
  *            tt_round's output); out[i].ranks receive the rounded ranks.
- *   streams  nstreams cudaStream_t handles (caller-owned).
- * Returns when every train is done (all streams synchronised).  On the first failing
- * train the remaining ones are not started and its status is returned. */
+ *   workspace/ws_bytes  device scratch of tt_apply_round_batched_workspace_size bytes.
+ * Returns when every train is done (stream synchronised); a failing train's status is
+ * returned (TT_ERR_NUMERIC for a Jacobi sweep cap or non-finite values). */
 int tt_apply_round_batched(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, double eps,
                            int64_t max_rank, int32_t prec, tt_train* out, void* workspace,
                            size_t ws_bytes, void* const* streams, int32_t nstreams);

@@ -276,12 +276,13 @@ def tt_eval_backward(x: TT, digits: torch.Tensor, dvalues: torch.Tensor, stream=
 
 
 def tt_apply_round_batched(Ws: list, xs: list, eps: float, max_rank: int = 0, prec: int | None = None,
-                           nstreams: int = 8, workspace: torch.Tensor | None = None,
+                           nstreams: int = 5, workspace: torch.Tensor | None = None,
                            streams: list | None = None):
     """Apply each W[i] to x[i] and round, for many trains at once (tt_apply_round_batched).
 
-    Returns the list of rounded TTs.  The library runs `nstreams` worker threads on as
-    many CUDA streams; every buffer comes from torch.
+    Returns the list of rounded TTs.  The trains advance in lock-step inside the library on
+    the first stream; up to four more streams run the size classes of the bond SVDs side by
+    side.  Every buffer comes from torch.
     """
     lib = load()
     n = len(xs)

@@ -445,7 +445,8 @@ size_t tt_apply_round_batched_workspace_size(int32_t n, const tt_mpo* W, const t
   if (n <= 0 || !W || !x || nstreams < 1) return 0;
   for (int i = 0; i < n; ++i)
     if (check_train(&x[i], "x") != TT_OK || validate_mpo(&W[i], &x[i]) != TT_OK) return 0;
-  return batched_slice_bytes(n, W, x, prec) * (size_t)nstreams;
+  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return 0;
+  return batched_workspace_bytes(n, W, x, prec);
 }
 
 int tt_apply_round_batched(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, double eps,
@@ -457,6 +458,14 @@ int tt_apply_round_batched(int32_t n, const tt_mpo* W, const tt_train* x, tt_tra
     if (!W || !x || !y || !out) return fail(TT_ERR_ARG, "tt_apply_round_batched: NULL descriptor array");
     if (nstreams < 1 || !streams) return fail(TT_ERR_ARG, "tt_apply_round_batched: no streams");
     if (!workspace) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: workspace is NULL");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(TT_ERR_ARG, "tt_apply_round_batched: eps must be finite and >= 0");
+    if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return fail(TT_ERR_ARG, "tt_apply_round_batched: bad prec");
+    for (int i = 0; i < n; ++i) {
+      if (prec == TT_PREC_FP64 && x[i].dtype != TT_F64)
+        return fail(TT_ERR_DTYPE, "tt_apply_round_batched: TT_PREC_FP64 needs TT_F64 cores");
+      if (prec == TT_PREC_MIXED && x[i].dtype != TT_F32)
+        return fail(TT_ERR_DTYPE, "tt_apply_round_batched: TT_PREC_MIXED needs TT_F32 cores");
+    }
     for (int i = 0; i < n; ++i) {
       TT_TRY(check_train(&x[i], "x"));
       TT_TRY(validate_mpo(&W[i], &x[i]));

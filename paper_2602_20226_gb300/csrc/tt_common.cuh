@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
 #include <stdint.h>
 
 #include <string>
@@ -166,6 +169,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
   __syncthreads();
   return s_ok != 0;
 }
+
+// ------------------------------------------------------------ batched job arrays
+// Per-launch job descriptors of the batched driver: staged in a pinned host ring and
+// copied asynchronously into a device region carved from the caller's workspace.
+// reset() may be called only when the stream has consumed every pushed array (after
+// a stream synchronisation).
+struct JobArena {
+  char* dev = nullptr;
+  char* host = nullptr;  // pinned
+  size_t cap = 0, off = 0;
+  template <typename J>
+  const J* push(const std::vector<J>& v, cudaStream_t s) {
+    const size_t bytes = v.size() * sizeof(J);
+    const size_t o = (off + 255) & ~size_t(255);
+    if (o + bytes > cap) return nullptr;
+    if (bytes) {
+      std::memcpy(host + o, v.data(), bytes);
+      if (cudaMemcpyAsync(dev + o, host + o, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return nullptr;
+    }
+    off = o + bytes;
+    return reinterpret_cast<const J*>(dev + o);
+  }
+  void reset() { off = 0; }
+};
 
 // --------------------------------------------------------------- small types
 

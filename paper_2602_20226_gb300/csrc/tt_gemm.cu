@@ -26,14 +26,12 @@ namespace {
 
 constexpr int BK = 16, NT = 256;
 
-// BM x BN tile, 16 x 16 threads, (BM / 16) x (BN / 16) outputs per thread.
+// BM x BN tile (bx, by) of C, 16 x 16 threads, (BM / 16) x (BN / 16) outputs per thread.
 template <int BM, int BN, typename TA, typename TB, typename TC>
-__global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, double alpha,
-                                                       const TA* __restrict__ A, int64_t sam,
-                                                       int64_t sak, const TB* __restrict__ B,
-                                                       int64_t sbk, int64_t sbn, double beta,
-                                                       TC* __restrict__ C, int64_t scm,
-                                                       int64_t scn) {
+__device__ __forceinline__ void gemm_tile(int M, int N, int K, double alpha, const TA* __restrict__ A,
+                                          int64_t sam, int64_t sak, const TB* __restrict__ B, int64_t sbk,
+                                          int64_t sbn, double beta, TC* __restrict__ C, int64_t scm,
+                                          int64_t scn, int bx, int by) {
   // FP32 operands and output: compensated FP32 (Dot2); anything else in FP64
   constexpr bool kDot2 = std::is_same<TA, float>::value && std::is_same<TB, float>::value &&
                          std::is_same<TC, float>::value;
@@ -42,7 +40,7 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
   __shared__ Acc Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = by * BM, n0 = bx * BN;
   constexpr int TM = BM / 16, TN = BN / 16;
   Acc acc[TM][TN], cmp[TM][TN];  // cmp: the collected rounding errors (Dot2 only)
 #pragma unroll
@@ -130,6 +128,25 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, doub
   }
 }
 
+template <int BM, int BN, typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, double alpha,
+                                                       const TA* __restrict__ A, int64_t sam,
+                                                       int64_t sak, const TB* __restrict__ B,
+                                                       int64_t sbk, int64_t sbn, double beta,
+                                                       TC* __restrict__ C, int64_t scm,
+                                                       int64_t scn) {
+  gemm_tile<BM, BN>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, blockIdx.x, blockIdx.y);
+}
+
+// One GEMM per blockIdx.z; tiles outside a job's M x N exit at once.
+template <int BM, int BN, typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(NT) gemm_batched_kernel(const GemmJob<TA, TB, TC>* __restrict__ jobs) {
+  const GemmJob<TA, TB, TC> j = jobs[blockIdx.z];
+  if ((int)blockIdx.y * BM >= j.M || (int)blockIdx.x * BN >= j.N || j.K <= 0) return;
+  gemm_tile<BM, BN>(j.M, j.N, j.K, j.alpha, j.A, j.sam, j.sak, j.B, j.sbk, j.sbn, j.beta, j.C, j.scm, j.scn,
+                    blockIdx.x, blockIdx.y);
+}
+
 template <typename TC>
 __global__ void scale_kernel(int M, int N, double beta, TC* C, int64_t scm, int64_t scn) {
   const int64_t total = (int64_t)M * N;
@@ -174,10 +191,29 @@ int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t
   return TT_OK;
 }
 
+template <typename TA, typename TB, typename TC>
+int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, int M_max, int N_max,
+                 int64_t tiles64) {
+  if (njobs <= 0 || M_max <= 0 || N_max <= 0) return TT_OK;
+  if (njobs > 65535) return fail(TT_ERR_UNSUPPORTED, "gemm_batched: too many jobs");
+  if (tiles64 >= num_sms()) {
+    dim3 grid((unsigned)ceil_div(N_max, 64), (unsigned)ceil_div(M_max, 64), (unsigned)njobs);
+    if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm_batched: M too large");
+    gemm_batched_kernel<64, 64, TA, TB, TC><<<grid, NT, 0, s>>>(d_jobs);
+  } else {
+    dim3 grid((unsigned)ceil_div(N_max, 32), (unsigned)ceil_div(M_max, 32), (unsigned)njobs);
+    if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm_batched: M too large");
+    gemm_batched_kernel<32, 32, TA, TB, TC><<<grid, NT, 0, s>>>(d_jobs);
+  }
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
 #define TT_GEMM_INST(TA, TB, TC)                                                           \
   template int gemm<TA, TB, TC>(cudaStream_t, int, int, int, double, const TA*, int64_t, \
                                 int64_t, const TB*, int64_t, int64_t, double, TC*, int64_t, \
-                                int64_t);
+                                int64_t);                                                  \
+  template int gemm_batched<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, int, int, int64_t);
 TT_GEMM_INST(double, double, double)
 TT_GEMM_INST(double, double, float)
 TT_GEMM_INST(double, float, double)

@@ -14,6 +14,23 @@ template <typename TA, typename TB, typename TC>
 int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t sam, int64_t sak,
          const TB* B, int64_t sbk, int64_t sbn, double beta, TC* C, int64_t scm, int64_t scn);
 
+// One C = alpha A B + beta C of a batch (strides as in gemm); beta == 0 never reads C.
+template <typename TA, typename TB, typename TC>
+struct GemmJob {
+  const TA* A;
+  const TB* B;
+  TC* C;
+  int64_t sam, sak, sbk, sbn, scm, scn;
+  int M, N, K;
+  double alpha, beta;
+};
+
+// All jobs of d_jobs (device array) in one launch; M_max / N_max bound every job's M / N,
+// tiles64 = sum over jobs of their 64 x 64 tile counts (picks the tile size).
+template <typename TA, typename TB, typename TC>
+int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, int M_max, int N_max,
+                 int64_t tiles64);
+
 // FP32 GEMM on the tensor cores, TF32 with a 3-term hi/lo split (tt_gemm_tc.cu).
 // acc64: sum the per-K-block tensor-core partials in FP64 registers.
 int gemm_tf32x3(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,

@@ -92,6 +92,31 @@ template <typename T>
 int copy_matrix(cudaStream_t s, const T* src, int p, int n, T* dst);
 
 int convert_f64_to_f32(cudaStream_t s, const double* a, long long n, float* b);
+
+// ---- batched maps (tt_batch_ops.cu): dst(i, j) = op(src(i, j)) for i < rows, j < cols,
+// src(i, j) = src[i sr + j sc], dst(i, j) = dst[i dr + j dc]; one job per train.
+enum MapOp : int {
+  MAP_COPY = 0,
+  MAP_UPPER = 1,  // zero below the diagonal (i > j)
+  MAP_NS = 2      // 1.5 [i == j] - 0.5 src (the Newton-Schulz factor)
+};
+struct MapJob {
+  const void* src;
+  void* dst;
+  int rows, cols;
+  int64_t sr, sc, dr, dc;
+  int op;
+};
+template <typename TS, typename TD>
+int map_batched(cudaStream_t s, int nj, const MapJob* d_jobs, int64_t max_elems);
+
+struct NormJob {
+  const void* src;  // n contiguous values
+  int64_t n;
+  double* out;      // ||src||_2 in FP64
+};
+template <typename T>
+int norm_batched(cudaStream_t s, int nj, const NormJob* d_jobs);
 int newton_schulz_h(cudaStream_t s, float* G, int n);  // G <- 1.5 I - 0.5 G
 
 }  // namespace tt

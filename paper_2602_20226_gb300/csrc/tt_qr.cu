@@ -22,10 +22,9 @@ namespace tt {
 namespace {
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda, int m, int j0,
-                                                      int jb, T* __restrict__ tau,
-                                                      T* __restrict__ Tm, int ldt,
-                                                      T* __restrict__ Vb, int ldv, bool staged) {
+__device__ __forceinline__ void panel_body(T* __restrict__ A, int lda, int m, int j0, int jb,
+                                           T* __restrict__ tau, T* __restrict__ Tm, int ldt,
+                                           T* __restrict__ Vb, int ldv, bool staged) {
   constexpr int NW = NT / 32;
   extern __shared__ unsigned char panel_raw[];
   __shared__ T red[NW][33];
@@ -141,6 +140,28 @@ __global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda
     const int r = e % jb, cc = e / jb;
     Tm[r + (int64_t)cc * ldt] = Ts[r][cc];
   }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) qr_panel_kernel(T* __restrict__ A, int lda, int m, int j0,
+                                                      int jb, T* __restrict__ tau,
+                                                      T* __restrict__ Tm, int ldt,
+                                                      T* __restrict__ Vb, int ldv, bool staged) {
+  panel_body<T, NT>(A, lda, m, j0, jb, tau, Tm, ldt, Vb, ldv, staged);
+}
+
+// Batched: the panel at column j0 of every job (one CTA per job), staged in shared
+// memory when mr x jb fits in smem_cap bytes.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) qr_panel_batched_kernel(const QrJob<T>* __restrict__ jobs, int j0,
+                                                              int nb, size_t smem_cap) {
+  const QrJob<T> J = jobs[blockIdx.x];
+  const int p = min(J.m, J.n);
+  if (j0 >= p) return;
+  const int jb = min(nb, p - j0);
+  const bool staged = (size_t)(J.m - j0) * jb * sizeof(T) <= smem_cap;
+  panel_body<T, NT>(J.A, J.lda, J.m, j0, jb, J.tau, J.tmat + (int64_t)(j0 / nb) * nb * nb, nb, J.vbuf, J.ldv,
+                    staged);
 }
 
 // The same panel factorisation spread over a thread-block cluster of CS CTAs: CTA c
@@ -289,14 +310,13 @@ __global__ void __launch_bounds__(NT) qr_panel_cluster_kernel(T* __restrict__ A,
 // the small-M half of applying the block reflector I - V T V^T (op(T) = T^T when
 // building R, T when building Q).  V (mr x jb) and A (mr x nc) are column-major.
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) reflector_w_kernel(const T* __restrict__ V, int ldv,
-                                                         const T* __restrict__ A, int lda, int mr,
-                                                         int jb, const T* __restrict__ Tm, int ldt,
-                                                         bool transpose_t, T* __restrict__ W2) {
+__device__ __forceinline__ void reflector_w_body(const T* __restrict__ V, int ldv, const T* __restrict__ A,
+                                                 int lda, int mr, int jb, const T* __restrict__ Tm, int ldt,
+                                                 bool transpose_t, T* __restrict__ W2, int c) {
   constexpr int NW = NT / 32;
   __shared__ T red[NW][33];
   __shared__ T w[32];
-  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* a = A + (int64_t)c * lda;
   T acc[32];
 #pragma unroll
@@ -325,6 +345,46 @@ __global__ void __launch_bounds__(NT) reflector_w_kernel(const T* __restrict__ V
       for (int q = tid; q < jb; ++q) v += Tm[tid + (int64_t)q * ldt] * w[q];
     }
     W2[tid + (int64_t)c * jb] = v;
+  }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) reflector_w_kernel(const T* __restrict__ V, int ldv,
+                                                         const T* __restrict__ A, int lda, int mr,
+                                                         int jb, const T* __restrict__ Tm, int ldt,
+                                                         bool transpose_t, T* __restrict__ W2) {
+  reflector_w_body<T, NT>(V, ldv, A, lda, mr, jb, Tm, ldt, transpose_t, W2, blockIdx.x);
+}
+
+// Batched W2 of the panel at j0 (blockIdx.y = job, blockIdx.x = column): the trailing
+// update of the QR (formq = false) or the update of the thin Q being formed.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) reflector_w_batched_kernel(const QrJob<T>* __restrict__ jobs, int j0,
+                                                                 int nb, bool formq) {
+  const QrJob<T> J = jobs[blockIdx.y];
+  const int p = min(J.m, J.n);
+  if (j0 >= p) return;
+  const int jb = min(nb, p - j0), mr = J.m - j0, c = blockIdx.x;
+  const T* V = J.vbuf + j0 + (int64_t)j0 * J.ldv;
+  const T* Tm = J.tmat + (int64_t)(j0 / nb) * nb * nb;
+  if (!formq) {
+    if (c >= J.n - (j0 + jb)) return;
+    reflector_w_body<T, NT>(V, J.ldv, J.A + j0 + (int64_t)(j0 + jb) * J.lda, J.lda, mr, jb, Tm, nb, true, J.w2, c);
+  } else {
+    if (c >= p - j0) return;
+    reflector_w_body<T, NT>(V, J.ldv, J.Q + j0 + (int64_t)j0 * J.ldq, J.ldq, mr, jb, Tm, nb, false, J.w2, c);
+  }
+}
+
+template <typename T>
+__global__ void init_thin_q_batched_kernel(const QrJob<T>* __restrict__ jobs) {
+  const QrJob<T> J = jobs[blockIdx.y];
+  const int p = min(J.m, J.n);
+  const int64_t total = (int64_t)J.m * p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % J.m), c = (int)(e / J.m);
+    J.Q[i + (int64_t)c * J.ldq] = (i == c) ? T(1) : T(0);
   }
 }
 
@@ -435,6 +495,114 @@ int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq) {
   return TT_OK;
 }
 
+template <typename T>
+int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
+                           JobArena& arena) {
+  const int nj = (int)hj.size();
+  if (nj == 0) return TT_OK;
+  if (nj > 65535) return fail(TT_ERR_UNSUPPORTED, "householder_qr_batched: too many jobs");
+  static int configured[2] = {-1, -1};
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (configured[sizeof(T) == 8] != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(qr_panel_batched_kernel<T, 512>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
+    configured[sizeof(T) == 8] = dev;
+  }
+  int p_max = 0, m_max = 0, n_max = 0;
+  for (const auto& J : hj) {
+    p_max = std::max(p_max, std::min(J.m, J.n));
+    m_max = std::max(m_max, J.m);
+    n_max = std::max(n_max, J.n);
+  }
+  const int npanels = (int)ceil_div(p_max, nb);
+  // the rank-nb updates A_t -= V W2 of every panel of every job, uploaded once
+  std::vector<GemmJob<T, T, T>> g((size_t)npanels * nj);
+  std::vector<int64_t> tiles(npanels, 0);
+  for (int pn = 0; pn < npanels; ++pn) {
+    const int j0 = pn * nb;
+    for (int q = 0; q < nj; ++q) {
+      const QrJob<T>& J = hj[q];
+      GemmJob<T, T, T>& G = g[(size_t)pn * nj + q];
+      G = GemmJob<T, T, T>{};
+      const int p = std::min(J.m, J.n);
+      if (j0 >= p) continue;
+      const int jb = std::min(nb, p - j0), mr = J.m - j0, nt = J.n - (j0 + jb);
+      if (nt <= 0) continue;
+      G = GemmJob<T, T, T>{J.vbuf + j0 + (int64_t)j0 * J.ldv, J.w2, J.A + j0 + (int64_t)(j0 + jb) * J.lda,
+                           1, J.ldv, 1, jb, 1, J.lda, mr, nt, jb, -1.0, 1.0};
+      tiles[pn] += ceil_div(mr, 64) * ceil_div(nt, 64);
+    }
+  }
+  const GemmJob<T, T, T>* dg = arena.push(g, s);
+  if (!dg) return fail(TT_ERR_WORKSPACE, "householder_qr_batched: job arena full");
+  for (int pn = 0; pn < npanels; ++pn) {
+    const int j0 = pn * nb;
+    const size_t smem = std::min(kPanelSmem, (size_t)(m_max - j0) * nb * sizeof(T));
+    qr_panel_batched_kernel<T, 512><<<nj, 512, smem, s>>>(d_jobs, j0, nb, smem);
+    TT_LAUNCH_CHECK();
+    const int nt_max = n_max - j0 - 1;
+    if (nt_max <= 0 || tiles[pn] == 0) continue;
+    reflector_w_batched_kernel<T, 256><<<dim3((unsigned)nt_max, (unsigned)nj), 256, 0, s>>>(d_jobs, j0, nb, false);
+    TT_LAUNCH_CHECK();
+    TT_TRY((gemm_batched<T, T, T>(s, nj, dg + (size_t)pn * nj, m_max - j0, nt_max, tiles[pn])));
+  }
+  return TT_OK;
+}
+
+template <typename T>
+int form_thin_q_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
+                        JobArena& arena) {
+  const int nj = (int)hj.size();
+  if (nj == 0) return TT_OK;
+  int p_max = 0, m_max = 0;
+  int64_t qmax = 1;
+  for (const auto& J : hj) {
+    const int p = std::min(J.m, J.n);
+    p_max = std::max(p_max, p);
+    m_max = std::max(m_max, J.m);
+    qmax = std::max<int64_t>(qmax, (int64_t)J.m * p);
+  }
+  init_thin_q_batched_kernel<T><<<dim3((unsigned)std::min<int64_t>(ceil_div(qmax, 256), 1024), (unsigned)nj), 256,
+                                  0, s>>>(d_jobs);
+  TT_LAUNCH_CHECK();
+  const int npanels = (int)ceil_div(p_max, nb);
+  std::vector<GemmJob<T, T, T>> g((size_t)npanels * nj);
+  std::vector<int64_t> tiles(npanels, 0);
+  for (int pn = 0; pn < npanels; ++pn) {
+    const int j0 = pn * nb;
+    for (int q = 0; q < nj; ++q) {
+      const QrJob<T>& J = hj[q];
+      GemmJob<T, T, T>& G = g[(size_t)pn * nj + q];
+      G = GemmJob<T, T, T>{};
+      const int p = std::min(J.m, J.n);
+      if (j0 >= p) continue;
+      const int jb = std::min(nb, p - j0), mr = J.m - j0, nc = p - j0;
+      G = GemmJob<T, T, T>{J.vbuf + j0 + (int64_t)j0 * J.ldv, J.w2, J.Q + j0 + (int64_t)j0 * J.ldq,
+                           1, J.ldv, 1, jb, 1, J.ldq, mr, nc, jb, -1.0, 1.0};
+      tiles[pn] += ceil_div(mr, 64) * ceil_div(nc, 64);
+    }
+  }
+  const GemmJob<T, T, T>* dg = arena.push(g, s);
+  if (!dg) return fail(TT_ERR_WORKSPACE, "form_thin_q_batched: job arena full");
+  for (int pn = npanels - 1; pn >= 0; --pn) {
+    const int j0 = pn * nb;
+    reflector_w_batched_kernel<T, 256><<<dim3((unsigned)(p_max - j0), (unsigned)nj), 256, 0, s>>>(d_jobs, j0, nb,
+                                                                                                  true);
+    TT_LAUNCH_CHECK();
+    TT_TRY((gemm_batched<T, T, T>(s, nj, dg + (size_t)pn * nj, m_max - j0, p_max - j0, tiles[pn])));
+  }
+  return TT_OK;
+}
+
+template int householder_qr_batched<double>(cudaStream_t, const std::vector<QrJob<double>>&, const QrJob<double>*,
+                                            int, JobArena&);
+template int householder_qr_batched<float>(cudaStream_t, const std::vector<QrJob<float>>&, const QrJob<float>*,
+                                           int, JobArena&);
+template int form_thin_q_batched<double>(cudaStream_t, const std::vector<QrJob<double>>&, const QrJob<double>*,
+                                         int, JobArena&);
+template int form_thin_q_batched<float>(cudaStream_t, const std::vector<QrJob<float>>&, const QrJob<float>*,
+                                        int, JobArena&);
 template int householder_qr<double>(cudaStream_t, double*, int, int, int, QrWork<double>&);
 template int householder_qr<float>(cudaStream_t, float*, int, int, int, QrWork<float>&);
 template int form_thin_q<double>(cudaStream_t, const QrWork<double>&, double*, int);

@@ -1,6 +1,8 @@
 // Householder QR used by the rounding sweeps.
 #pragma once
 
+#include <vector>
+
 #include "tt_common.cuh"
 #include "tt_gemm.cuh"
 
@@ -28,5 +30,28 @@ int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w);
 // Thin Q (m x min(m,n), column-major, ld ldq) from the reflectors of the last QR.
 template <typename T>
 int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq);
+
+// ---- batched forms: one job per train of a batch, the panels of all jobs in lock-step
+template <typename T>
+struct QrJob {
+  T* A;  // m x n, column-major, ld lda: QR'd in place
+  int m, n, lda;
+  T* tau;
+  T* tmat;  // T factors, [panel][nb][nb]
+  T* vbuf;  // explicit reflectors, ld ldv
+  int ldv;
+  T* w2;    // [nb * max(n, min(m, n))]
+  T* Q;     // form_thin_q_batched: m x min(m, n), ld ldq
+  int ldq;
+};
+
+// hj: the jobs on the host (sizes, for the launch shapes and the update GEMMs);
+// d_jobs: the same array in device memory.
+template <typename T>
+int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
+                           JobArena& arena);
+template <typename T>
+int form_thin_q_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
+                        JobArena& arena);
 
 }  // namespace tt

@@ -20,91 +20,6 @@ namespace tt {
 
 namespace {
 
-struct Carver {
-  char* base;
-  size_t off = 0;
-  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
-  template <typename U>
-  U* take(size_t n) {
-    off = (off + 255) & ~size_t(255);
-    U* p = base ? reinterpret_cast<U*>(base + off) : nullptr;
-    off += n * sizeof(U);
-    return p;
-  }
-};
-
-struct Dims {
-  int L = 0;
-  int64_t S_max = 1;  // largest core (elements)
-  int64_t r_max = 1;  // largest rank
-};
-
-Dims dims_of(const tt_train* x) {
-  Dims D;
-  D.L = x->L;
-  for (int k = 0; k < x->L; ++k) {
-    D.S_max = std::max<int64_t>(D.S_max, x->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1]);
-    D.r_max = std::max<int64_t>(D.r_max, std::max(x->ranks[k], x->ranks[k + 1]));
-  }
-  return D;
-}
-
-template <typename T>
-struct Bufs {
-  T *A = nullptr, *Q = nullptr, *tmp = nullptr, *Rbuf = nullptr, *vsel = nullptr, *F = nullptr;
-  float *X32 = nullptr, *V32 = nullptr, *G32 = nullptr;  // mixed-form bond SVD
-  double* W64 = nullptr;
-  QrWork<T> qr;
-  SvdWork sv;
-};
-
-template <typename T>
-size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
-  B.A = c.take<T>(D.S_max);
-  B.Q = c.take<T>(D.S_max);
-  B.tmp = c.take<T>(D.S_max);
-  B.qr.nb = nb;
-  B.qr.vbuf = c.take<T>(D.S_max);
-  B.qr.tau = c.take<T>(D.r_max + 32);
-  B.qr.tmat = c.take<T>((size_t)nb * nb * (ceil_div(D.r_max, nb) + 1));
-  B.qr.w1 = c.take<T>((size_t)nb * D.r_max);
-  B.qr.w2 = c.take<T>((size_t)nb * D.r_max);
-  B.Rbuf = c.take<T>((size_t)D.r_max * D.r_max);
-  B.vsel = c.take<T>((size_t)D.r_max * D.r_max);
-  B.F = c.take<T>((size_t)D.r_max * D.r_max);
-  B.sv.X = c.take<double>((size_t)D.r_max * D.r_max);
-  if (std::is_same<T, float>::value) {
-    B.X32 = c.take<float>((size_t)D.r_max * D.r_max);
-    B.V32 = c.take<float>((size_t)D.r_max * D.r_max);
-    B.G32 = c.take<float>((size_t)D.r_max * D.r_max);
-    B.W64 = c.take<double>((size_t)D.r_max * D.r_max);
-  }
-  B.sv.sigma = c.take<double>(D.r_max);
-  B.sv.perm = c.take<int>(D.r_max);
-  B.sv.rank = c.take<int>(1);
-  B.sv.bar = c.take<unsigned>(2);
-  B.sv.rot = c.take<unsigned>(SvdWork::kMaxSweeps);
-  B.sv.status = c.take<unsigned>(1);
-  B.sv.sweeps = c.take<int>(1);
-  B.sv.norm = c.take<double>(1);
-  B.sv.epoch = c.take<unsigned>((size_t)D.r_max + 2);
-  return c.off + 256;
-}
-
-template <typename T>
-int panel_width() {
-  return sizeof(T) == 8 ? 16 : 32;
-}
-
-// Relative resolution of the mixed form's bond SVD (see the truncation call).
-constexpr double kMixedSigmaFloor = 1.0 / (1 << 22);
-
-template <typename T>
-double jacobi_tol(int nrow) {
-  // columns are treated as orthogonal once |x_a . x_b| <= tol ||x_a|| ||x_b||
-  return std::sqrt((double)std::max(nrow, 1)) * 2.220446049250313e-16;
-}
-
 // Opt-in phase timer (environment variable TT_TRACE=1): synchronises the stream at
 // phase boundaries and prints the wall time per phase to stderr at the end.
 struct PhaseTimer {
@@ -284,10 +199,11 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
       // C_k <- Q and C_{k+1} <- R C_{k+1} represent the same tensor as the SVD factors
       // would (they differ by an orthogonal gauge), and the SVD is skipped.
       bool certified = false;
-      if (tall && (max_rank <= 0 || max_rank >= p) && 64 * (size_t)p <= 200 * 1024) {
+      // (the certificate subtracts p u ||R||_F, so it cannot succeed unless p u < delta / ||x||)
+      const double unit = sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+      if (tall && (max_rank <= 0 || max_rank >= p) && 64 * (size_t)p <= 200 * 1024 && p * unit < delta_scale) {
         pe = prof.begin();
-        TT_TRY(certify_full_rank(s, B.sv, B.sv.X, p, p, delta_scale,
-                                 sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07));
+        TT_TRY(certify_full_rank(s, B.sv, B.sv.X, p, p, delta_scale, unit));
         prof.end(pe, PROF_CERT, (double)p * p * p / 3.0);
         int flag = 0;
         TT_TRY(read_back(s, B.sv.rank, &flag, sizeof(int)));

@@ -408,7 +408,7 @@ __global__ void identity_f32_kernel(float* V, int n, int ldv) {
 // sigma_j = ||X[:, j]||, sorted descending (stable), and the truncation rank:
 // the smallest r >= 1 with sqrt(sum_{j >= r} sigma_j^2) <= delta, accumulated from
 // the smallest singular value upwards, then capped at max_rank.
-__global__ void __launch_bounds__(1024) svd_truncate_kernel(
+__device__ __forceinline__ void svd_truncate_body(
     const double* X, int nrow, int ncol, int ldx, const double* norm, double delta_scale,
     long long max_rank, double rel_floor, double* sig_sorted, int* perm, int* rank_out,
     unsigned* status) {
@@ -466,6 +466,14 @@ __global__ void __launch_bounds__(1024) svd_truncate_kernel(
   }
 }
 
+__global__ void __launch_bounds__(1024) svd_truncate_kernel(
+    const double* X, int nrow, int ncol, int ldx, const double* norm, double delta_scale,
+    long long max_rank, double rel_floor, double* sig_sorted, int* perm, int* rank_out,
+    unsigned* status) {
+  svd_truncate_body(X, nrow, ncol, ldx, norm, delta_scale, max_rank, rel_floor, sig_sorted, perm, rank_out,
+                    status);
+}
+
 // U[:, t] = X[:, perm[t]] / sigma_t  (nrow x r, column-major); zero column if sigma_t = 0
 template <typename TO>
 __global__ void svd_left_kernel(const double* X, int nrow, int ldx, const int* perm,
@@ -485,10 +493,9 @@ __global__ void svd_left_kernel(const double* X, int nrow, int ldx, const int* p
 // of R + dR with |dR| <= p u |R|, so the certificate subtracts p u ||R||_F.  If
 // sigma_min > delta, no singular value can be dropped (the smallest tail already
 // exceeds delta) and the bond keeps its full rank.
-__global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int p, int ldr,
-                                                           double* colsq) {
+__device__ __forceinline__ void rinv_colnorm_body(const double* R, int p, int ldr, double* colsq, int bx) {
   const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int j = bx * 8 + (threadIdx.x >> 5);
   if (j >= p) return;
   // z = R^{-1} e_j: z_j = 1/R_jj, z_i = -(sum_{l=i+1..j} R_il z_l) / R_ii for i < j,
   // kept in this warp's slice of shared memory.
@@ -510,10 +517,14 @@ __global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int 
   if (lane == 0) colsq[j] = nrm2;
 }
 
+__global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int p, int ldr,
+                                                           double* colsq) {
+  rinv_colnorm_body(R, p, ldr, colsq, blockIdx.x);
+}
+
 // flag = 1 if 1/||R^{-1}||_F - p u ||R||_F > 1.01 delta (certified full rank), else 0.
-__global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, int ldr,
-                                                       const double* colsq, const double* norm,
-                                                       double delta_scale, double unit, int* flag) {
+__device__ __forceinline__ void certify_body(const double* R, int p, int ldr, const double* colsq,
+                                             const double* norm, double delta_scale, double unit, int* flag) {
   __shared__ double scratch[32];
   double inv2 = 0.0, r2 = 0.0;
   for (int j = threadIdx.x; j < p; j += blockDim.x) inv2 += colsq[j];
@@ -531,6 +542,265 @@ __global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, i
     const double lower = (isfinite(inv2) && inv2 > 0.0) ? 1.0 / sqrt(inv2) : 0.0;
     const double slack = (double)p * unit * sqrt(r2);
     *flag = (lower - slack > 1.01 * delta) ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, int ldr,
+                                                       const double* colsq, const double* norm,
+                                                       double delta_scale, double unit, int* flag) {
+  certify_body(R, p, ldr, colsq, norm, delta_scale, unit, flag);
+}
+
+// ------------------------------------------------------------------ batched forms
+// One job per train of a batch; every kernel below takes the job from its block index.
+
+__global__ void __launch_bounds__(256) rinv_colnorm_batched_kernel(const SvdJob* __restrict__ jobs) {
+  const SvdJob& J = jobs[blockIdx.y];
+  if ((int)blockIdx.x * 8 >= J.n) return;
+  rinv_colnorm_body(J.X, J.n, J.ldx, J.sigma, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) certify_batched_kernel(const SvdJob* __restrict__ jobs, double delta_scale,
+                                                               double unit) {
+  const SvdJob& J = jobs[blockIdx.x];
+  certify_body(J.X, J.n, J.ldx, J.sigma, J.norm, delta_scale, unit, J.rank);
+}
+
+__global__ void __launch_bounds__(1024) svd_truncate_batched_kernel(const SvdJob* __restrict__ jobs,
+                                                                    double delta_scale, long long max_rank,
+                                                                    double rel_floor) {
+  const SvdJob& J = jobs[blockIdx.x];
+  svd_truncate_body(J.X, J.n, J.n, J.ldx, J.norm, delta_scale, max_rank, rel_floor, J.sigma, J.perm, J.rank,
+                    J.status);
+}
+
+// Cluster forms: one thread-block cluster of CS CTAs per job (clusters are co-scheduled,
+// so the per-job barriers are hardware cluster barriers).  CTA `rank` of a cluster takes
+// every CS-th pair (FP64) or group pair (FP32) of a round; the columns stay in global
+// memory (read and written through L2) and the cluster barrier after each round orders
+// those accesses between the CTAs.  The sweep's rotation count is summed over the
+// cluster through distributed shared memory.
+__device__ __forceinline__ unsigned cluster_sum_u32(unsigned* slot, int cs, unsigned* bcast) {
+  // *slot: this CTA's count (already final); returns the cluster total in every thread
+  cluster_sync_all();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(slot);
+    for (int r = 0; r < cs; ++r) {
+      unsigned ra, v;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(r));
+      asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+      t += v;
+    }
+    *bcast = t;
+  }
+  cluster_sync_all();  // every CTA has read every slot before any resets its own
+  return *bcast;
+}
+
+template <int NT, int TPL, int CS>
+__global__ void __launch_bounds__(NT) jacobi_f64_cluster_kernel(const SvdJob* __restrict__ jobs, double delta_scale,
+                                                                int max_sweeps) {
+  const int rank = (int)(blockIdx.x % CS);
+  const SvdJob& J = jobs[blockIdx.x / CS];
+  const int ncol = J.n, nrow = J.n;
+  if (ncol <= 0) return;  // the whole cluster leaves together
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = rank * NW + warp, GW = CS * NW;
+  const double tol = sqrt((double)ncol) * 2.220446049250313e-16;
+  const double nl = delta_scale > 0.0 ? delta_scale * __ldcg(J.norm) / sqrt(2.0 * ncol) : 0.0;
+  const double negl = nl * nl;
+  const int N = ncol + (ncol & 1), npairs = N / 2;
+  __shared__ unsigned s_rot, s_tot;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < N - 1; ++rnd) {
+      for (int q = gw; q < npairs; q += GW) {
+        int a, b;
+        if (q == 0) {
+          a = rnd;
+          b = N - 1;
+        } else {
+          a = (rnd + q) % (N - 1);
+          b = (rnd - q + N - 1) % (N - 1);
+        }
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+        }
+        if (b < ncol && rotate_pair<TPL>(J.X + (int64_t)a * J.ldx, J.X + (int64_t)b * J.ldx, nrow, lane, tol, negl) &&
+            lane == 0)
+          atomicAdd(&s_rot, 1u);
+      }
+      __syncthreads();
+      cluster_sync_all();
+    }
+    converged = cluster_sum_u32(&s_rot, CS, &s_tot) == 0u;
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    *J.sweeps = sweep;
+    if (!converged) atomicOr(J.status, (unsigned)ST_NONCONVERGED);
+  }
+}
+
+// FP32 rotation of global columns (xa, xb) of X and (va, vb) of V (length n each),
+// in chunks of 32 * TPL values held in registers; loads of a chunk are issued together.
+template <int TPL>
+__device__ __forceinline__ bool rotate_pair_f32_global(float* __restrict__ xa, float* __restrict__ xb,
+                                                       float* __restrict__ va, float* __restrict__ vb, int n,
+                                                       int lane, float tol, float negl) {
+  constexpr int CH = 32 * TPL;
+  float ra[TPL], rb[TPL], pa[TPL], pb[TPL];
+  float al = 0.f, be = 0.f, ga = 0.f;
+  // V's columns are read after the rotation is known (fetching them with X's raised the
+  // register count and lowered the number of resident warps, which cost more than the
+  // saved L2 round trip when many jobs share the GPU)
+  constexpr bool one = false;
+  for (int i0 = 0; i0 < n; i0 += CH) {
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = i0 + lane + 32 * t;
+      ra[t] = i < n ? __ldcg(xa + i) : 0.f;
+      rb[t] = i < n ? __ldcg(xb + i) : 0.f;
+      if (one) {
+        pa[t] = i < n ? __ldcg(va + i) : 0.f;
+        pb[t] = i < n ? __ldcg(vb + i) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      al = fmaf(ra[t], ra[t], al);
+      be = fmaf(rb[t], rb[t], be);
+      ga = fmaf(ra[t], rb[t], ga);
+    }
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (al < negl && be < negl) return false;
+  if (!(ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
+  const float zeta = (be - al) / (2.f * ga);
+  const float tn = (fabsf(zeta) > 1e18f) ? 0.5f / zeta
+                                         : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = 1.f / sqrtf(1.f + tn * tn);
+  const float s = c * tn;
+  if (s == 0.f) return false;
+  for (int i0 = 0; i0 < n; i0 += CH) {
+    if (n > CH) {
+#pragma unroll
+      for (int t = 0; t < TPL; ++t) {
+        const int i = i0 + lane + 32 * t;
+        ra[t] = i < n ? __ldcg(xa + i) : 0.f;
+        rb[t] = i < n ? __ldcg(xb + i) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = i0 + lane + 32 * t;
+      if (i < n) {
+        __stcg(xa + i, c * ra[t] - s * rb[t]);
+        __stcg(xb + i, s * ra[t] + c * rb[t]);
+      }
+    }
+  }
+  for (int i0 = 0; i0 < n; i0 += CH) {
+    if (!one) {
+#pragma unroll
+      for (int t = 0; t < TPL; ++t) {
+        const int i = i0 + lane + 32 * t;
+        pa[t] = i < n ? __ldcg(va + i) : 0.f;
+        pb[t] = i < n ? __ldcg(vb + i) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+      const int i = i0 + lane + 32 * t;
+      if (i < n) {
+        __stcg(va + i, c * pa[t] - s * pb[t]);
+        __stcg(vb + i, s * pa[t] + c * pb[t]);
+      }
+    }
+  }
+  return true;
+}
+
+// FP32 one-sided Jacobi with accumulated V, plain round-robin ordering (as the FP64
+// cluster kernel): the CS x NT / 32 warps of a job's cluster take the pairs of a round,
+// one cluster barrier per round.
+template <int NT, int TPL, int CS>
+__global__ void __launch_bounds__(NT) jacobi_f32rr_cluster_kernel(const SvdJob* __restrict__ jobs,
+                                                                  int max_sweeps) {
+  const int rank = (int)(blockIdx.x % CS);
+  const SvdJob& J = jobs[blockIdx.x / CS];
+  const int n = J.n;
+  if (n <= 0) return;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gw = rank * NW + warp, GW = CS * NW;
+  float* X = J.X32;
+  float* V = J.V32;
+  const int ld = J.ld32;
+  for (int64_t e = (int64_t)rank * blockDim.x + tid; e < (int64_t)n * n; e += (int64_t)CS * blockDim.x) {
+    const int i = (int)(e % n), c = (int)(e / n);
+    V[i + (int64_t)c * ld] = (i == c) ? 1.f : 0.f;
+  }
+  const float tol = 8.f * sqrtf((float)n) * 5.9604645e-8f;
+  const float nl = (float)(__ldcg(J.norm) / (double)(1 << 22) / sqrt(2.0 * n));
+  const float negl = nl * nl;
+  const int N = n + (n & 1), npairs = N / 2;
+  __shared__ unsigned s_rot, s_tot;
+  if (tid == 0) s_rot = 0;
+  __syncthreads();
+  cluster_sync_all();
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int rnd = 0; rnd < N - 1; ++rnd) {
+      for (int q = gw; q < npairs; q += GW) {
+        int a, b;
+        if (q == 0) {
+          a = rnd;
+          b = N - 1;
+        } else {
+          a = (rnd + q) % (N - 1);
+          b = (rnd - q + N - 1) % (N - 1);
+        }
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+        }
+        if (b < n && rotate_pair_f32_global<TPL>(X + (int64_t)a * ld, X + (int64_t)b * ld, V + (int64_t)a * ld,
+                                                 V + (int64_t)b * ld, n, lane, tol, negl) &&
+            lane == 0)
+          atomicAdd(&s_rot, 1u);
+      }
+      __syncthreads();
+      cluster_sync_all();
+    }
+    converged = cluster_sum_u32(&s_rot, CS, &s_tot) == 0u;
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+  }
+  if (rank == 0 && tid == 0) *J.sweeps = converged ? sweep : -1;
+}
+
+template <typename TO>
+__global__ void svd_left_batched_kernel(const SvdJob* __restrict__ jobs) {
+  const SvdJob& J = jobs[blockIdx.y];
+  const int r = J.r, nrow = J.n;
+  TO* U = static_cast<TO*>(J.U);
+  const int64_t total = (int64_t)nrow * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nrow), t = (int)(e / nrow);
+    const double sg = J.sigma[t];
+    U[e] = sg > 0.0 ? (TO)(__ldcg(J.X + i + (int64_t)J.perm[t] * J.ldx) / sg) : TO(0);
   }
 }
 
@@ -707,6 +977,167 @@ int svd_left_vectors(cudaStream_t s, const SvdWork& w, int nrow, int r, TO* U) {
   return TT_OK;
 }
 
+// ---------------------------------------------------------------- batched launchers
+int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale, double unit) {
+  if (nj <= 0 || n_max <= 0) return TT_OK;
+  const size_t smem = 8 * (size_t)n_max * sizeof(double);
+  if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "certify_batched: rank too large");
+  static int configured = -1;
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (configured != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+    configured = dev;
+  }
+  rinv_colnorm_batched_kernel<<<dim3((unsigned)ceil_div(n_max, 8), (unsigned)nj), 256, smem, s>>>(d_jobs);
+  TT_LAUNCH_CHECK();
+  certify_batched_kernel<<<nj, 1024, 0, s>>>(d_jobs, delta_scale, unit);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+namespace {
+
+template <typename K, typename... Args>
+int launch_cluster(cudaStream_t s, K kernel, int cs, int nj, int nt, size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nj * cs));
+  cfg.blockDim = dim3((unsigned)nt);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kernel, args...));
+  note_launch();
+  return TT_OK;
+}
+
+template <typename K>
+int allow_cluster16(K kernel) {
+  TT_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  return TT_OK;
+}
+
+template <int CS>
+int f64_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale, int max_sweeps) {
+  if (CS > 8) {
+    static int configured = -1;
+    int dev = 0;
+    TT_CUDA_CHECK(cudaGetDevice(&dev));
+    if (configured != dev) {
+      TT_TRY(allow_cluster16(jacobi_f64_cluster_kernel<256, 4, CS>));
+      TT_TRY(allow_cluster16(jacobi_f64_cluster_kernel<256, 8, CS>));
+      TT_TRY(allow_cluster16(jacobi_f64_cluster_kernel<256, 16, CS>));
+      TT_TRY(allow_cluster16(jacobi_f64_cluster_kernel<256, 0, CS>));
+      configured = dev;
+    }
+  }
+  if (n_max <= 128)
+    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 4, CS>, CS, nj, 256, 0, d_jobs, delta_scale, max_sweeps);
+  if (n_max <= 256)
+    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 8, CS>, CS, nj, 256, 0, d_jobs, delta_scale, max_sweeps);
+  if (n_max <= 512)
+    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 16, CS>, CS, nj, 256, 0, d_jobs, delta_scale,
+                          max_sweeps);
+  return launch_cluster(s, jacobi_f64_cluster_kernel<256, 0, CS>, CS, nj, 256, 0, d_jobs, delta_scale, max_sweeps);
+}
+
+template <int CS>
+int f32_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int max_sweeps) {
+  if (CS > 8) {
+    static int configured = -1;
+    int dev = 0;
+    TT_CUDA_CHECK(cudaGetDevice(&dev));
+    if (configured != dev) {
+      TT_TRY(allow_cluster16(jacobi_f32rr_cluster_kernel<256, 4, CS>));
+      TT_TRY(allow_cluster16(jacobi_f32rr_cluster_kernel<256, 8, CS>));
+      TT_TRY(allow_cluster16(jacobi_f32rr_cluster_kernel<256, 16, CS>));
+      TT_TRY(allow_cluster16(jacobi_f32rr_cluster_kernel<256, 20, CS>));
+      configured = dev;
+    }
+  }
+  if (n_max <= 128)
+    return launch_cluster(s, jacobi_f32rr_cluster_kernel<256, 4, CS>, CS, nj, 256, 0, d_jobs, max_sweeps);
+  if (n_max <= 256)
+    return launch_cluster(s, jacobi_f32rr_cluster_kernel<256, 8, CS>, CS, nj, 256, 0, d_jobs, max_sweeps);
+  if (n_max <= 512)
+    return launch_cluster(s, jacobi_f32rr_cluster_kernel<256, 16, CS>, CS, nj, 256, 0, d_jobs, max_sweeps);
+  return launch_cluster(s, jacobi_f32rr_cluster_kernel<256, 20, CS>, CS, nj, 256, 0, d_jobs, max_sweeps);
+}
+
+}  // namespace
+
+int svd_cluster_size(int n, bool fp64) {
+  // about two to four pairs per warp and round, 8 warps per CTA; the FP64 kernel is bound
+  // by the FP64 pipe of its SMs and gains from 16 CTAs on the largest factors, the FP32
+  // one (latency-bound, many jobs side by side) does not
+  if (n <= 64) return 1;
+  if (n <= 128) return 2;
+  if (n <= 256) return 4;
+  if (n <= 320 || !fp64) return 8;
+  return 16;
+}
+
+int jacobi_f64_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
+                       int max_sweeps, int cs) {
+  if (nj <= 0 || n_max <= 0) return TT_OK;
+  switch (cs) {
+    case 1: return f64_cluster<1>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
+    case 2: return f64_cluster<2>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
+    case 4: return f64_cluster<4>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
+    case 8: return f64_cluster<8>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
+    case 16: return f64_cluster<16>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
+  }
+  return fail(TT_ERR_ARG, "jacobi_f64_batched: cluster size");
+}
+
+int jacobi_f32_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int max_sweeps, int cs) {
+  if (nj <= 0 || n_max <= 0) return TT_OK;
+  switch (cs) {
+    case 1: return f32_cluster<1>(s, nj, d_jobs, n_max, max_sweeps);
+    case 2: return f32_cluster<2>(s, nj, d_jobs, n_max, max_sweeps);
+    case 4: return f32_cluster<4>(s, nj, d_jobs, n_max, max_sweeps);
+    case 8: return f32_cluster<8>(s, nj, d_jobs, n_max, max_sweeps);
+    case 16: return f32_cluster<16>(s, nj, d_jobs, n_max, max_sweeps);
+  }
+  return fail(TT_ERR_ARG, "jacobi_f32_batched: cluster size");
+}
+
+int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
+                         int64_t max_rank, double rel_floor) {
+  if (nj <= 0 || n_max <= 0) return TT_OK;
+  const size_t smem = 2 * (size_t)n_max * sizeof(double);
+  if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "svd_truncate_batched: bond rank too large");
+  static int configured = -1;
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (configured != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(svd_truncate_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+    configured = dev;
+  }
+  svd_truncate_batched_kernel<<<nj, 1024, smem, s>>>(d_jobs, delta_scale, (long long)max_rank, rel_floor);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+template <typename TO>
+int svd_left_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int64_t max_elems) {
+  if (nj <= 0 || max_elems <= 0) return TT_OK;
+  svd_left_batched_kernel<TO>
+      <<<dim3((unsigned)std::min<int64_t>(ceil_div(max_elems, 256), 1024), (unsigned)nj), 256, 0, s>>>(d_jobs);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+template int svd_left_batched<double>(cudaStream_t, int, const SvdJob*, int64_t);
+template int svd_left_batched<float>(cudaStream_t, int, const SvdJob*, int64_t);
 template int svd_left_vectors<double>(cudaStream_t, const SvdWork&, int, int, double*);
 template int svd_left_vectors<float>(cudaStream_t, const SvdWork&, int, int, float*);
 

@@ -46,6 +46,36 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
 int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale,
                       double unit);
 
+// ---- batched forms (one job per train of a batch, jobs in device memory)
+struct SvdJob {
+  double* X;        // n x n FP64 factor, column-major, ld ldx (rotated in place / W)
+  int n, ldx;
+  float* X32;       // mixed form: FP32 copy of the factor and the accumulated rotations
+  float* V32;
+  int ld32;
+  double* sigma;
+  int* perm;
+  int* rank;        // truncation rank (or the certificate flag)
+  unsigned* status;
+  int* sweeps;
+  const double* norm;
+  int r;            // svd_left_batched: columns to gather into U (n x r)
+  void* U;
+};
+int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale, double unit);
+// Bond SVDs of a batch, one thread-block cluster of cs CTAs per job, all
+// jobs of similar size: svd_cluster_size(n, fp64) picks cs (1 to 16) for bond rank n.
+int svd_cluster_size(int n, bool fp64);
+int jacobi_f64_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
+                       int max_sweeps, int cs);
+// *sweeps = -1 when a job's FP32 sweeps did not settle (its caller finishes it in FP64)
+int jacobi_f32_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int max_sweeps, int cs);
+int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
+                         int64_t max_rank, double rel_floor);
+template <typename TO>
+int svd_left_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int64_t max_elems);
+size_t jacobi_block_smem_gs(int gs, int nrow, int ncol);
+
 // U (nrow x r, column-major) = X[:, perm[:r]] / sigma[:r]  (left singular vectors).
 template <typename TO>
 int svd_left_vectors(cudaStream_t s, const SvdWork& w, int nrow, int r, TO* U);
