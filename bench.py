@@ -226,7 +226,7 @@ def run_ours(args):
     # ---- secondary workloads (reported beside the main line)
     extra = {}
     if not args.no_extra:
-        extra["batched"] = bench_batched(tt, dev, Wm, n_tt=args.batch_trains)
+        extra["batched"] = bench_batched(tt, dev, Wm, n_tt=args.batch_trains, rank=rank, world=world)
         extra["eval"] = bench_eval(tt, dev)
 
     # ---- end to end: pinned host cores in, rounded cores out, through the public API
@@ -304,20 +304,25 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def bench_batched(tt, dev, warm, n_tt=128, nstreams=5, n_err=4):
+def bench_batched(tt, dev, warm, n_tt=128, nstreams=5, n_err=4, rank=0, world=1):
     """Uneven batch (L ~ U[20,60], rank ~ U[8,128], MPO rank ~ U{3,4,5}), eps = 1e-6, through
     tt_apply_round_batched (lock-step over the trains): the mixed form (FP32 cores) against
     the FP64 form on the same trains, and the mixed results' error against the oracle on
-    the n_err cheapest trains."""
+    the n_err cheapest trains.  Under torchrun every rank rounds its share of the trains
+    (longest-processing-time split, no exchange); the value is all ranks' nominal flops over
+    the slowest rank's time."""
     import torch
+    import torch.distributed as dist
 
     from oracle import core as ocore
     from paper_2602_20226_gb300 import inputs
     from paper_2602_20226_gb300.flops import apply_flops, round_flops
+    from paper_2602_20226_gb300.shard import lpt_partition
 
-    shapes = inputs.batch_shapes(4, n_tt)
-    xs = [inputs.random_tt(4000 + i, L, 2, r) for i, (L, r, a) in enumerate(shapes)]
-    ws = [inputs.random_mpo(4500 + i, L, 2, a) for i, (L, r, a) in enumerate(shapes)]
+    all_shapes = inputs.batch_shapes(4, n_tt)
+    mine = lpt_partition(all_shapes, world)[rank]
+    xs = [inputs.random_tt(4000 + i, all_shapes[i][0], 2, all_shapes[i][1]) for i in mine]
+    ws = [inputs.random_mpo(4500 + i, all_shapes[i][0], 2, all_shapes[i][2]) for i in mine]
     streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
     res = {}
     outs_by_form = {}
@@ -326,6 +331,8 @@ def bench_batched(tt, dev, warm, n_tt=128, nstreams=5, n_err=4):
         W = [tt.MPO.from_numpy([c.astype(np.float32) for c in w], device=dev, dtype=dt) for w in ws]
         tt.tt_apply_round_batched(W[:8], X[:8], 1e-6, nstreams=nstreams, streams=streams)  # warm-up
         torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         outs = tt.tt_apply_round_batched(W, X, 1e-6, nstreams=nstreams, streams=streams)
         torch.cuda.synchronize(dev)
@@ -334,22 +341,30 @@ def bench_batched(tt, dev, warm, n_tt=128, nstreams=5, n_err=4):
         for x, w, o in zip(X, W, outs):
             yr = [a * b for a, b in zip(w.ranks, x.ranks)]
             flops += apply_flops(w.ranks, x.ranks, x.dims) + round_flops(yr, o.ranks, x.dims)["total"]
+        if world > 1:
+            t = torch.tensor([sec, flops], dtype=torch.float64, device=dev)
+            mx = t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            sec, flops = float(mx[0].item()), float(t[1].item())
         res[form] = {"value": round(flops / sec / 1e9, 3), "unit": "GFLOP/s", "seconds": round(sec, 3),
                      "nominal_flops": flops}
         outs_by_form[form] = outs
     # error of the mixed results against the oracle (inputs are the FP32 values in FP64)
-    order = sorted(range(n_tt), key=lambda i: shapes[i][0] * (shapes[i][1] * shapes[i][2]) ** 3)[:n_err]
+    order = sorted(range(len(mine)),
+                   key=lambda q: all_shapes[mine[q]][0] * (all_shapes[mine[q]][1] * all_shapes[mine[q]][2]) ** 3)
     errs = []
-    for i in order:
-        x64 = [c.astype(np.float32).astype(np.float64) for c in xs[i]]
-        w64 = [c.astype(np.float32).astype(np.float64) for c in ws[i]]
+    for q in order[:n_err]:
+        x64 = [c.astype(np.float32).astype(np.float64) for c in xs[q]]
+        w64 = [c.astype(np.float32).astype(np.float64) for c in ws[q]]
         ref = ocore.round_tt(ocore.apply_mpo(w64, x64), 1e-6)
-        errs.append(ocore.rel_err(outs_by_form["mixed"][i].numpy(), ref))
+        errs.append(ocore.rel_err(outs_by_form["mixed"][q].numpy(), ref))
     return {"workload": f"{n_tt} trains, L~U[20,60], rank~U[8,128], MPO rank~U{{3,4,5}}, eps=1e-6, "
                         "lock-step batched driver (host-timed, one batch)",
             "mixed": res["mixed"], "fp64": res["fp64"],
             "speedup_mixed_vs_fp64": round(res["fp64"]["seconds"] / res["mixed"]["seconds"], 3),
-            "mixed_rel_err_vs_oracle_max": max(errs), "mixed_err_sample": f"{n_err} cheapest trains"}
+            "mixed_rel_err_vs_oracle_max": max(errs) if errs else None,
+            "mixed_err_sample": f"{n_err} cheapest trains (of rank {rank})"}
 
 
 def bench_eval(tt, dev, n=1 << 20, L=40, r=64):

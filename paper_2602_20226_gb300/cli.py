@@ -7,6 +7,11 @@ Builds the seeded quantics TT (n_dims x bits sites, interleaved, d = 2, cores N(
 scaled by 1/sqrt(d r)), applies the Dirichlet Laplacian MPO of that grid (rank 3 in 1D,
 5 in 2D, 7 in 3D) and rounds the result, `--repeat` times, printing the wall time of
 each repetition and the output ranks.  `--op hadamard` rounds x (.) x instead.
+
+    python -m paper_2602_20226_gb300.cli --batch 512 --form mixed --eps 1e-6
+
+runs tt_apply_round_batched on the uneven batch instead: trains with L ~ U[20, 60],
+ranks ~ U[8, 128], each with its own random MPO of rank 3..5 (seed 4).
 """
 from __future__ import annotations
 
@@ -28,7 +33,10 @@ def main(argv=None) -> None:
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=0, help="trains of the uneven batch (0: one train)")
     a = ap.parse_args(argv)
+    if a.batch > 0:
+        return _batch(a)
 
     dtype = torch.float64 if a.form == "fp64" else torch.float32
     prec = _abi.TT_PREC_FP64 if a.form == "fp64" else _abi.TT_PREC_MIXED
@@ -47,6 +55,25 @@ def main(argv=None) -> None:
         torch.cuda.synchronize()
         print(f"[{i}] {a.form} {a.op} round: {(time.perf_counter() - t) * 1e3:.2f} ms, "
               f"max rank {max(Y.ranks)} -> {max(Z.ranks)}, norm {nrm:.12e}", flush=True)
+
+
+
+def _batch(a) -> None:
+    import numpy as np
+
+    dtype = torch.float64 if a.form == "fp64" else torch.float32
+    shapes = inputs.batch_shapes(4, a.batch)
+    X = [api.TT.from_numpy([c.astype(np.float32) for c in inputs.random_tt(4000 + i, L, 2, r)], dtype=dtype)
+         for i, (L, r, _) in enumerate(shapes)]
+    W = [api.MPO.from_numpy([c.astype(np.float32) for c in inputs.random_mpo(4500 + i, L, 2, m)], dtype=dtype)
+         for i, (L, _, m) in enumerate(shapes)]
+    for i in range(a.repeat):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        outs = api.tt_apply_round_batched(W, X, a.eps)
+        torch.cuda.synchronize()
+        print(f"[{i}] {a.form} batch of {a.batch}: {(time.perf_counter() - t) * 1e3:.1f} ms, "
+              f"max rank {max(max(o.ranks) for o in outs)}", flush=True)
 
 
 if __name__ == "__main__":

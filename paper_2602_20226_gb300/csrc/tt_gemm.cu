@@ -27,15 +27,17 @@ namespace {
 constexpr int BK = 16, NT = 256;
 
 // BM x BN tile (bx, by) of C, 16 x 16 threads, (BM / 16) x (BN / 16) outputs per thread.
-template <int BM, int BN, typename TA, typename TB, typename TC>
+// COMP: compensated (Dot2) accumulation when all operands are FP32.
+template <int BM, int BN, typename TA, typename TB, typename TC, bool COMP = true>
 __device__ __forceinline__ void gemm_tile(int M, int N, int K, double alpha, const TA* __restrict__ A,
                                           int64_t sam, int64_t sak, const TB* __restrict__ B, int64_t sbk,
                                           int64_t sbn, double beta, TC* __restrict__ C, int64_t scm,
                                           int64_t scn, int bx, int by) {
   // FP32 operands and output: compensated FP32 (Dot2); anything else in FP64
-  constexpr bool kDot2 = std::is_same<TA, float>::value && std::is_same<TB, float>::value &&
-                         std::is_same<TC, float>::value;
-  using Acc = std::conditional_t<kDot2, float, double>;
+  constexpr bool kAllF32 = std::is_same<TA, float>::value && std::is_same<TB, float>::value &&
+                          std::is_same<TC, float>::value;
+  constexpr bool kDot2 = COMP && kAllF32;
+  using Acc = std::conditional_t<kAllF32, float, double>;  // FP32 operands: FP32 (plain or Dot2)
   __shared__ Acc As[BK][BM + 1];
   __shared__ Acc Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -128,23 +130,24 @@ __device__ __forceinline__ void gemm_tile(int M, int N, int K, double alpha, con
   }
 }
 
-template <int BM, int BN, typename TA, typename TB, typename TC>
+template <int BM, int BN, typename TA, typename TB, typename TC, bool COMP>
 __global__ void __launch_bounds__(NT) gemm_simt_kernel(int M, int N, int K, double alpha,
                                                        const TA* __restrict__ A, int64_t sam,
                                                        int64_t sak, const TB* __restrict__ B,
                                                        int64_t sbk, int64_t sbn, double beta,
                                                        TC* __restrict__ C, int64_t scm,
                                                        int64_t scn) {
-  gemm_tile<BM, BN>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, blockIdx.x, blockIdx.y);
+  gemm_tile<BM, BN, TA, TB, TC, COMP>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, blockIdx.x,
+                                      blockIdx.y);
 }
 
 // One GEMM per blockIdx.z; tiles outside a job's M x N exit at once.
-template <int BM, int BN, typename TA, typename TB, typename TC>
+template <int BM, int BN, typename TA, typename TB, typename TC, bool COMP>
 __global__ void __launch_bounds__(NT) gemm_batched_kernel(const GemmJob<TA, TB, TC>* __restrict__ jobs) {
   const GemmJob<TA, TB, TC> j = jobs[blockIdx.z];
   if ((int)blockIdx.y * BM >= j.M || (int)blockIdx.x * BN >= j.N || j.K <= 0) return;
-  gemm_tile<BM, BN>(j.M, j.N, j.K, j.alpha, j.A, j.sam, j.sak, j.B, j.sbk, j.sbn, j.beta, j.C, j.scm, j.scn,
-                    blockIdx.x, blockIdx.y);
+  gemm_tile<BM, BN, TA, TB, TC, COMP>(j.M, j.N, j.K, j.alpha, j.A, j.sam, j.sak, j.B, j.sbk, j.sbn, j.beta, j.C,
+                                      j.scm, j.scn, blockIdx.x, blockIdx.y);
 }
 
 template <typename TC>
@@ -160,9 +163,9 @@ __global__ void scale_kernel(int M, int N, double beta, TC* C, int64_t scm, int6
 
 }  // namespace
 
-template <typename TA, typename TB, typename TC>
-int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t sam, int64_t sak,
-         const TB* B, int64_t sbk, int64_t sbn, double beta, TC* C, int64_t scm, int64_t scn) {
+template <typename TA, typename TB, typename TC, bool COMP>
+int gemm_launch(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t sam, int64_t sak,
+                const TB* B, int64_t sbk, int64_t sbn, double beta, TC* C, int64_t scm, int64_t scn) {
   if (M <= 0 || N <= 0) return TT_OK;
   if (K <= 0) {
     if (beta == 1.0) return TT_OK;
@@ -179,12 +182,12 @@ int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t
   if (big >= num_sms()) {
     dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
     if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm: M too large");
-    gemm_simt_kernel<64, 64, TA, TB, TC>
+    gemm_simt_kernel<64, 64, TA, TB, TC, COMP>
         <<<grid, NT, 0, s>>>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
   } else {
     dim3 grid((unsigned)ceil_div(N, 32), (unsigned)ceil_div(M, 32));
     if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm: M too large");
-    gemm_simt_kernel<32, 32, TA, TB, TC>
+    gemm_simt_kernel<32, 32, TA, TB, TC, COMP>
         <<<grid, NT, 0, s>>>(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
   }
   TT_LAUNCH_CHECK();
@@ -192,18 +195,26 @@ int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t
 }
 
 template <typename TA, typename TB, typename TC>
+int gemm(cudaStream_t s, int M, int N, int K, double alpha, const TA* A, int64_t sam, int64_t sak,
+         const TB* B, int64_t sbk, int64_t sbn, double beta, TC* C, int64_t scm, int64_t scn) {
+  return gemm_launch<TA, TB, TC, true>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+}
+
+template <typename TA, typename TB, typename TC>
 int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, int M_max, int N_max,
-                 int64_t tiles64) {
+                 int64_t tiles64, bool compensated) {
   if (njobs <= 0 || M_max <= 0 || N_max <= 0) return TT_OK;
   if (njobs > 65535) return fail(TT_ERR_UNSUPPORTED, "gemm_batched: too many jobs");
   if (tiles64 >= num_sms()) {
     dim3 grid((unsigned)ceil_div(N_max, 64), (unsigned)ceil_div(M_max, 64), (unsigned)njobs);
     if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm_batched: M too large");
-    gemm_batched_kernel<64, 64, TA, TB, TC><<<grid, NT, 0, s>>>(d_jobs);
+    if (compensated) gemm_batched_kernel<64, 64, TA, TB, TC, true><<<grid, NT, 0, s>>>(d_jobs);
+    else gemm_batched_kernel<64, 64, TA, TB, TC, false><<<grid, NT, 0, s>>>(d_jobs);
   } else {
     dim3 grid((unsigned)ceil_div(N_max, 32), (unsigned)ceil_div(M_max, 32), (unsigned)njobs);
     if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm_batched: M too large");
-    gemm_batched_kernel<32, 32, TA, TB, TC><<<grid, NT, 0, s>>>(d_jobs);
+    if (compensated) gemm_batched_kernel<32, 32, TA, TB, TC, true><<<grid, NT, 0, s>>>(d_jobs);
+    else gemm_batched_kernel<32, 32, TA, TB, TC, false><<<grid, NT, 0, s>>>(d_jobs);
   }
   TT_LAUNCH_CHECK();
   return TT_OK;
@@ -213,7 +224,7 @@ int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, i
   template int gemm<TA, TB, TC>(cudaStream_t, int, int, int, double, const TA*, int64_t, \
                                 int64_t, const TB*, int64_t, int64_t, double, TC*, int64_t, \
                                 int64_t);                                                  \
-  template int gemm_batched<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, int, int, int64_t);
+  template int gemm_batched<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, int, int, int64_t, bool);
 TT_GEMM_INST(double, double, double)
 TT_GEMM_INST(double, double, float)
 TT_GEMM_INST(double, float, double)
@@ -237,7 +248,7 @@ int gemm_fast<float>(cudaStream_t s, int M, int N, int K, double alpha, const fl
                      int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
                      int64_t scm, int64_t scn, unsigned* status) {
   (void)status;
-  return gemm<float, float, float>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+  return gemm_launch<float, float, float, true>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
 }
 
 template <>

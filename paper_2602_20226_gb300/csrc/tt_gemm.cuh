@@ -27,9 +27,10 @@ struct GemmJob {
 
 // All jobs of d_jobs (device array) in one launch; M_max / N_max bound every job's M / N,
 // tiles64 = sum over jobs of their 64 x 64 tile counts (picks the tile size).
+// compensated: Dot2 accumulation when all operands are FP32 (plain FP32 FMA otherwise).
 template <typename TA, typename TB, typename TC>
 int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, int M_max, int N_max,
-                 int64_t tiles64);
+                 int64_t tiles64, bool compensated = true);
 
 // FP32 GEMM on the tensor cores, TF32 with a 3-term hi/lo split (tt_gemm_tc.cu).
 // acc64: sum the per-K-block tensor-core partials in FP64 registers.
@@ -46,8 +47,9 @@ int gemm_core(cudaStream_t s, int M, int N, int K, double alpha, const T* A, int
               const T* B, int64_t sbk, int64_t sbn, double beta, T* C, int64_t scm, int64_t scn,
               unsigned* status);
 
-// The GEMM inside the Householder QR of each form: FP64 -> SIMT DFMA; FP32 -> SIMT
-// with compensated (Dot2) accumulation, for the same reason as gemm_core.
+// The GEMM inside the Householder QR of each form: FP64 -> SIMT DFMA; FP32 -> SIMT with
+// compensated (Dot2) accumulation: with plain FP32 accumulation of the trailing updates
+// the error of 20..60-site trains at eps = 1e-6 rose from ~2e-6 to 4.6e-6.
 template <typename T>
 int gemm_fast(cudaStream_t s, int M, int N, int K, double alpha, const T* A, int64_t sam, int64_t sak,
               const T* B, int64_t sbk, int64_t sbn, double beta, T* C, int64_t scm, int64_t scn,

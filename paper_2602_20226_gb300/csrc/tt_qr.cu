@@ -495,6 +495,104 @@ int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq) {
   return TT_OK;
 }
 
+// The three GEMMs that apply the panel at j0 of every job to its trailing block X
+// (mr x nc, column-major, ld ldx):  W1 = V^T X,  W2 = op(T) W1,  X -= V W2.
+// W2 = op(T) V^T X is formed as two GEMMs rather than by one CTA per column: a CTA
+// per column re-reads the whole mr x jb reflector panel, which for hundreds of jobs at
+// once is tens of GB of L2 traffic per panel; the tiled GEMM reads it once per tile.
+template <typename T>
+struct PanelGemms {
+  std::vector<GemmJob<T, T, T>> w1, w2, up;
+  int64_t t1 = 0, t2 = 0, t3 = 0;
+  int m1 = 0, n1 = 0, m3 = 0;
+};
+
+template <typename T>
+void panel_gemm_jobs(const QrJob<T>& J, int j0, int nb, bool formq, PanelGemms<T>& G) {
+  const int p = std::min(J.m, J.n);
+  GemmJob<T, T, T> z{};
+  if (j0 >= p) {
+    G.w1.push_back(z);
+    G.w2.push_back(z);
+    G.up.push_back(z);
+    return;
+  }
+  const int jb = std::min(nb, p - j0), mr = J.m - j0;
+  T* X;
+  int ldx, nc;
+  if (!formq) {
+    X = J.A + j0 + (int64_t)(j0 + jb) * J.lda;
+    ldx = J.lda;
+    nc = J.n - (j0 + jb);
+  } else {
+    X = J.Q + j0 + (int64_t)j0 * J.ldq;
+    ldx = J.ldq;
+    nc = p - j0;
+  }
+  if (nc <= 0) {
+    G.w1.push_back(z);
+    G.w2.push_back(z);
+    G.up.push_back(z);
+    return;
+  }
+  const T* V = J.vbuf + j0 + (int64_t)j0 * J.ldv;
+  const T* Tm = J.tmat + (int64_t)(j0 / nb) * nb * nb;
+  // W1 (jb x nc, ld jb) = V^T X
+  G.w1.push_back(GemmJob<T, T, T>{V, X, J.w1, J.ldv, 1, 1, ldx, 1, jb, jb, nc, mr, 1.0, 0.0});
+  // W2 = T^T W1 (QR of A) or T W1 (building Q); T is upper triangular, zero below
+  if (!formq) G.w2.push_back(GemmJob<T, T, T>{Tm, J.w1, J.w2, nb, 1, 1, jb, 1, jb, jb, nc, jb, 1.0, 0.0});
+  else G.w2.push_back(GemmJob<T, T, T>{Tm, J.w1, J.w2, 1, nb, 1, jb, 1, jb, jb, nc, jb, 1.0, 0.0});
+  // X -= V W2
+  G.up.push_back(GemmJob<T, T, T>{V, J.w2, X, 1, J.ldv, 1, jb, 1, ldx, mr, nc, jb, -1.0, 1.0});
+  G.t1 += ceil_div(jb, 64) * ceil_div(nc, 64);
+  G.t2 += ceil_div(jb, 64) * ceil_div(nc, 64);
+  G.t3 += ceil_div(mr, 64) * ceil_div(nc, 64);
+  G.m1 = std::max(G.m1, jb);
+  G.n1 = std::max(G.n1, nc);
+  G.m3 = std::max(G.m3, mr);
+}
+
+// FP32: the three GEMMs, compensated (Dot2) - plain FP32 accumulation of the updates took
+// the error of 20..60-site trains at eps = 1e-6 from ~2e-6 to 4.6e-6.  FP64: W2 by the
+// reflector kernel (one CTA per column), then the update GEMM - measured faster in FP64,
+// where the work is bound by the FP64 pipe rather than by L2 traffic.
+template <typename T>
+int apply_panels(cudaStream_t s, const QrJob<T>* d_jobs, int nj, int nb, bool formq, int pn,
+                 const GemmJob<T, T, T>* d1, const GemmJob<T, T, T>* d2, const GemmJob<T, T, T>* d3,
+                 const std::vector<PanelGemms<T>>& meta) {
+  const PanelGemms<T>& M = meta[pn];
+  if (M.n1 <= 0) return TT_OK;
+  if (sizeof(T) == 4) {
+    TT_TRY((gemm_batched<T, T, T>(s, nj, d1 + (size_t)pn * nj, M.m1, M.n1, M.t1)));
+    TT_TRY((gemm_batched<T, T, T>(s, nj, d2 + (size_t)pn * nj, M.m1, M.n1, M.t2)));
+  } else {
+    reflector_w_batched_kernel<T, 256><<<dim3((unsigned)M.n1, (unsigned)nj), 256, 0, s>>>(d_jobs, pn * nb, nb,
+                                                                                          formq);
+    TT_LAUNCH_CHECK();
+  }
+  TT_TRY((gemm_batched<T, T, T>(s, nj, d3 + (size_t)pn * nj, M.m3, M.n1, M.t3)));
+  return TT_OK;
+}
+
+template <typename T>
+int build_panel_gemms(cudaStream_t s, const std::vector<QrJob<T>>& hj, int nb, bool formq, int npanels,
+                      JobArena& arena, std::vector<PanelGemms<T>>& meta, const GemmJob<T, T, T>** d1,
+                      const GemmJob<T, T, T>** d2, const GemmJob<T, T, T>** d3) {
+  meta.assign(npanels, PanelGemms<T>{});
+  std::vector<GemmJob<T, T, T>> a1, a2, a3;
+  for (int pn = 0; pn < npanels; ++pn) {
+    for (const auto& J : hj) panel_gemm_jobs(J, pn * nb, nb, formq, meta[pn]);
+    a1.insert(a1.end(), meta[pn].w1.begin(), meta[pn].w1.end());
+    a2.insert(a2.end(), meta[pn].w2.begin(), meta[pn].w2.end());
+    a3.insert(a3.end(), meta[pn].up.begin(), meta[pn].up.end());
+  }
+  *d1 = arena.push(a1, s);
+  *d2 = arena.push(a2, s);
+  *d3 = arena.push(a3, s);
+  if (!*d1 || !*d2 || !*d3) return fail(TT_ERR_WORKSPACE, "batched QR: job arena full");
+  return TT_OK;
+}
+
 template <typename T>
 int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
                            JobArena& arena) {
@@ -509,43 +607,21 @@ int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, cons
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
     configured[sizeof(T) == 8] = dev;
   }
-  int p_max = 0, m_max = 0, n_max = 0;
+  int p_max = 0, m_max = 0;
   for (const auto& J : hj) {
     p_max = std::max(p_max, std::min(J.m, J.n));
     m_max = std::max(m_max, J.m);
-    n_max = std::max(n_max, J.n);
   }
   const int npanels = (int)ceil_div(p_max, nb);
-  // the rank-nb updates A_t -= V W2 of every panel of every job, uploaded once
-  std::vector<GemmJob<T, T, T>> g((size_t)npanels * nj);
-  std::vector<int64_t> tiles(npanels, 0);
-  for (int pn = 0; pn < npanels; ++pn) {
-    const int j0 = pn * nb;
-    for (int q = 0; q < nj; ++q) {
-      const QrJob<T>& J = hj[q];
-      GemmJob<T, T, T>& G = g[(size_t)pn * nj + q];
-      G = GemmJob<T, T, T>{};
-      const int p = std::min(J.m, J.n);
-      if (j0 >= p) continue;
-      const int jb = std::min(nb, p - j0), mr = J.m - j0, nt = J.n - (j0 + jb);
-      if (nt <= 0) continue;
-      G = GemmJob<T, T, T>{J.vbuf + j0 + (int64_t)j0 * J.ldv, J.w2, J.A + j0 + (int64_t)(j0 + jb) * J.lda,
-                           1, J.ldv, 1, jb, 1, J.lda, mr, nt, jb, -1.0, 1.0};
-      tiles[pn] += ceil_div(mr, 64) * ceil_div(nt, 64);
-    }
-  }
-  const GemmJob<T, T, T>* dg = arena.push(g, s);
-  if (!dg) return fail(TT_ERR_WORKSPACE, "householder_qr_batched: job arena full");
+  std::vector<PanelGemms<T>> meta;
+  const GemmJob<T, T, T> *d1, *d2, *d3;
+  TT_TRY(build_panel_gemms(s, hj, nb, false, npanels, arena, meta, &d1, &d2, &d3));
   for (int pn = 0; pn < npanels; ++pn) {
     const int j0 = pn * nb;
     const size_t smem = std::min(kPanelSmem, (size_t)(m_max - j0) * nb * sizeof(T));
     qr_panel_batched_kernel<T, 512><<<nj, 512, smem, s>>>(d_jobs, j0, nb, smem);
     TT_LAUNCH_CHECK();
-    const int nt_max = n_max - j0 - 1;
-    if (nt_max <= 0 || tiles[pn] == 0) continue;
-    reflector_w_batched_kernel<T, 256><<<dim3((unsigned)nt_max, (unsigned)nj), 256, 0, s>>>(d_jobs, j0, nb, false);
-    TT_LAUNCH_CHECK();
-    TT_TRY((gemm_batched<T, T, T>(s, nj, dg + (size_t)pn * nj, m_max - j0, nt_max, tiles[pn])));
+    TT_TRY(apply_panels(s, d_jobs, nj, nb, false, pn, d1, d2, d3, meta));
   }
   return TT_OK;
 }
@@ -555,43 +631,21 @@ int form_thin_q_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const Q
                         JobArena& arena) {
   const int nj = (int)hj.size();
   if (nj == 0) return TT_OK;
-  int p_max = 0, m_max = 0;
+  int p_max = 0;
   int64_t qmax = 1;
   for (const auto& J : hj) {
     const int p = std::min(J.m, J.n);
     p_max = std::max(p_max, p);
-    m_max = std::max(m_max, J.m);
     qmax = std::max<int64_t>(qmax, (int64_t)J.m * p);
   }
   init_thin_q_batched_kernel<T><<<dim3((unsigned)std::min<int64_t>(ceil_div(qmax, 256), 1024), (unsigned)nj), 256,
                                   0, s>>>(d_jobs);
   TT_LAUNCH_CHECK();
   const int npanels = (int)ceil_div(p_max, nb);
-  std::vector<GemmJob<T, T, T>> g((size_t)npanels * nj);
-  std::vector<int64_t> tiles(npanels, 0);
-  for (int pn = 0; pn < npanels; ++pn) {
-    const int j0 = pn * nb;
-    for (int q = 0; q < nj; ++q) {
-      const QrJob<T>& J = hj[q];
-      GemmJob<T, T, T>& G = g[(size_t)pn * nj + q];
-      G = GemmJob<T, T, T>{};
-      const int p = std::min(J.m, J.n);
-      if (j0 >= p) continue;
-      const int jb = std::min(nb, p - j0), mr = J.m - j0, nc = p - j0;
-      G = GemmJob<T, T, T>{J.vbuf + j0 + (int64_t)j0 * J.ldv, J.w2, J.Q + j0 + (int64_t)j0 * J.ldq,
-                           1, J.ldv, 1, jb, 1, J.ldq, mr, nc, jb, -1.0, 1.0};
-      tiles[pn] += ceil_div(mr, 64) * ceil_div(nc, 64);
-    }
-  }
-  const GemmJob<T, T, T>* dg = arena.push(g, s);
-  if (!dg) return fail(TT_ERR_WORKSPACE, "form_thin_q_batched: job arena full");
-  for (int pn = npanels - 1; pn >= 0; --pn) {
-    const int j0 = pn * nb;
-    reflector_w_batched_kernel<T, 256><<<dim3((unsigned)(p_max - j0), (unsigned)nj), 256, 0, s>>>(d_jobs, j0, nb,
-                                                                                                  true);
-    TT_LAUNCH_CHECK();
-    TT_TRY((gemm_batched<T, T, T>(s, nj, dg + (size_t)pn * nj, m_max - j0, p_max - j0, tiles[pn])));
-  }
+  std::vector<PanelGemms<T>> meta;
+  const GemmJob<T, T, T> *d1, *d2, *d3;
+  TT_TRY(build_panel_gemms(s, hj, nb, true, npanels, arena, meta, &d1, &d2, &d3));
+  for (int pn = npanels - 1; pn >= 0; --pn) TT_TRY(apply_panels(s, d_jobs, nj, nb, true, pn, d1, d2, d3, meta));
   return TT_OK;
 }
 

@@ -40,6 +40,7 @@ struct QrJob {
   T* tmat;  // T factors, [panel][nb][nb]
   T* vbuf;  // explicit reflectors, ld ldv
   int ldv;
+  T* w1;    // [nb * max(n, min(m, n))]
   T* w2;    // [nb * max(n, min(m, n))]
   T* Q;     // form_thin_q_batched: m x min(m, n), ld ldq
   int ldq;

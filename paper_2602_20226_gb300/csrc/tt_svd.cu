@@ -648,29 +648,20 @@ __global__ void __launch_bounds__(NT) jacobi_f64_cluster_kernel(const SvdJob* __
   }
 }
 
-// FP32 rotation of global columns (xa, xb) of X and (va, vb) of V (length n each),
-// in chunks of 32 * TPL values held in registers; loads of a chunk are issued together.
+// FP32 rotation of the global columns (xa, xb) (length n) in chunks of 32 * TPL values held
+// in registers (loads of a chunk issued together).
 template <int TPL>
-__device__ __forceinline__ bool rotate_pair_f32_global(float* __restrict__ xa, float* __restrict__ xb,
-                                                       float* __restrict__ va, float* __restrict__ vb, int n,
+__device__ __forceinline__ bool rotate_pair_f32_global(float* __restrict__ xa, float* __restrict__ xb, int n,
                                                        int lane, float tol, float negl) {
   constexpr int CH = 32 * TPL;
-  float ra[TPL], rb[TPL], pa[TPL], pb[TPL];
+  float ra[TPL], rb[TPL];
   float al = 0.f, be = 0.f, ga = 0.f;
-  // V's columns are read after the rotation is known (fetching them with X's raised the
-  // register count and lowered the number of resident warps, which cost more than the
-  // saved L2 round trip when many jobs share the GPU)
-  constexpr bool one = false;
   for (int i0 = 0; i0 < n; i0 += CH) {
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
       const int i = i0 + lane + 32 * t;
       ra[t] = i < n ? __ldcg(xa + i) : 0.f;
       rb[t] = i < n ? __ldcg(xb + i) : 0.f;
-      if (one) {
-        pa[t] = i < n ? __ldcg(va + i) : 0.f;
-        pb[t] = i < n ? __ldcg(vb + i) : 0.f;
-      }
     }
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
@@ -708,30 +699,12 @@ __device__ __forceinline__ bool rotate_pair_f32_global(float* __restrict__ xa, f
       }
     }
   }
-  for (int i0 = 0; i0 < n; i0 += CH) {
-    if (!one) {
-#pragma unroll
-      for (int t = 0; t < TPL; ++t) {
-        const int i = i0 + lane + 32 * t;
-        pa[t] = i < n ? __ldcg(va + i) : 0.f;
-        pb[t] = i < n ? __ldcg(vb + i) : 0.f;
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < TPL; ++t) {
-      const int i = i0 + lane + 32 * t;
-      if (i < n) {
-        __stcg(va + i, c * pa[t] - s * pb[t]);
-        __stcg(vb + i, s * pa[t] + c * pb[t]);
-      }
-    }
-  }
   return true;
 }
 
-// FP32 one-sided Jacobi with accumulated V, plain round-robin ordering (as the FP64
-// cluster kernel): the CS x NT / 32 warps of a job's cluster take the pairs of a round,
-// one cluster barrier per round.
+// FP32 one-sided Jacobi (rotations not accumulated), plain round-robin ordering as the
+// FP64 cluster kernel: the CS x NT / 32 warps of a job's cluster take the pairs of a
+// round, one cluster barrier per round.  J.X32 ends with W = X J (sigma_j = ||W_j||).
 template <int NT, int TPL, int CS>
 __global__ void __launch_bounds__(NT) jacobi_f32rr_cluster_kernel(const SvdJob* __restrict__ jobs,
                                                                   int max_sweeps) {
@@ -743,12 +716,7 @@ __global__ void __launch_bounds__(NT) jacobi_f32rr_cluster_kernel(const SvdJob* 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gw = rank * NW + warp, GW = CS * NW;
   float* X = J.X32;
-  float* V = J.V32;
   const int ld = J.ld32;
-  for (int64_t e = (int64_t)rank * blockDim.x + tid; e < (int64_t)n * n; e += (int64_t)CS * blockDim.x) {
-    const int i = (int)(e % n), c = (int)(e / n);
-    V[i + (int64_t)c * ld] = (i == c) ? 1.f : 0.f;
-  }
   const float tol = 8.f * sqrtf((float)n) * 5.9604645e-8f;
   const float nl = (float)(__ldcg(J.norm) / (double)(1 << 22) / sqrt(2.0 * n));
   const float negl = nl * nl;
@@ -775,8 +743,7 @@ __global__ void __launch_bounds__(NT) jacobi_f32rr_cluster_kernel(const SvdJob* 
           a = b;
           b = t;
         }
-        if (b < n && rotate_pair_f32_global<TPL>(X + (int64_t)a * ld, X + (int64_t)b * ld, V + (int64_t)a * ld,
-                                                 V + (int64_t)b * ld, n, lane, tol, negl) &&
+        if (b < n && rotate_pair_f32_global<TPL>(X + (int64_t)a * ld, X + (int64_t)b * ld, n, lane, tol, negl) &&
             lane == 0)
           atomicAdd(&s_rot, 1u);
       }

@@ -68,7 +68,8 @@ int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, dou
 int svd_cluster_size(int n, bool fp64);
 int jacobi_f64_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
                        int max_sweeps, int cs);
-// *sweeps = -1 when a job's FP32 sweeps did not settle (its caller finishes it in FP64)
+// FP32 form: rotates J.X32 into W (rotations not accumulated); *sweeps = -1 when a job's
+// FP32 sweeps did not settle (its caller finishes it in FP64).
 int jacobi_f32_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int max_sweeps, int cs);
 int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
                          int64_t max_rank, double rel_floor);
