@@ -382,7 +382,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     for (int a = 0; a < na; ++a) {
       TrainState<T>& S = tr[act[a]];
       Bufs<T>& B = S.B;
-      sj[a] = SvdJob{B.sv.X, pp_[a], pp_[a], B.X32, B.V32, pp_[a], B.sv.sigma, B.sv.perm, B.sv.rank,
+      sj[a] = SvdJob{B.sv.X, pp_[a], pp_[a], B.X32, pp_[a], B.sv.sigma, B.sv.perm, B.sv.rank,
                      B.sv.status, B.sv.sweeps, B.sv.norm, 0, B.vsel};
     }
     // ---- certificate (tall bonds, max_rank not binding, when it can succeed at all:

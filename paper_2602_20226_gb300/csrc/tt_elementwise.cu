@@ -251,6 +251,11 @@ __global__ void f64_to_f32_kernel(const double* a, long long n, float* b) {
     b[e] = (float)a[e];
 }
 
+__global__ void f32_to_f64_kernel(const float* a, long long n, double* b) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    b[e] = (double)a[e];
+}
+
 // G <- 1.5 I - 0.5 G  (n x n, column-major): the Newton-Schulz factor for U^T U = G
 __global__ void ns_h_kernel(float* G, int n) {
   const long long total = (long long)n * n;
@@ -358,6 +363,12 @@ int frobenius_norm(cudaStream_t s, const T* a, long long n, double* out) {
 
 int convert_f64_to_f32(cudaStream_t s, const double* a, long long n, float* b) {
   f64_to_f32_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(a, n, b);
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
+int convert_f32_to_f64(cudaStream_t s, const float* a, long long n, double* b) {
+  f32_to_f64_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(a, n, b);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }

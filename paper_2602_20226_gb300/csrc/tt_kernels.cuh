@@ -92,6 +92,7 @@ template <typename T>
 int copy_matrix(cudaStream_t s, const T* src, int p, int n, T* dst);
 
 int convert_f64_to_f32(cudaStream_t s, const double* a, long long n, float* b);
+int convert_f32_to_f64(cudaStream_t s, const float* a, long long n, double* b);
 
 // ---- batched maps (tt_batch_ops.cu): dst(i, j) = op(src(i, j)) for i < rows, j < cols,
 // src(i, j) = src[i sr + j sc], dst(i, j) = dst[i dr + j dc]; one job per train.

@@ -223,21 +223,18 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         int sweeps32 = 0;
         const bool mixed_svd = std::is_same<T, float>::value && jacobi_block_smem(p, p) <= 200 * 1024;
         if (mixed_svd) {
-          // Mixed form: FP32 one-sided Jacobi with accumulated rotations V (block
-          // round-robin), then W = X V re-formed in FP64 from the FP64 copy of the factor.
-          // W's columns are orthogonal to eta ~ sqrt(p) 2^-24, so their FP64 norms give the
-          // singular values to O(eta^2) relative accuracy (the Gram matrix of W is diagonal
-          // up to eta), and sigma and the truncation decision are FP64.  The kept left
-          // vectors W_j / sigma_j are re-orthonormalised below.
+          // Mixed form: FP32 one-sided Jacobi (block round-robin, rotations not
+          // accumulated) rotates the FP32 copy X of the factor into W = X J; sigma_j = ||W_j||
+          // in FP64 and the truncation decision are FP64 (a one-sided Jacobi keeps each
+          // column's rounding error relative to that column), and the kept left vectors
+          // W_j / sigma_j are re-orthonormalised below.
           TT_TRY(convert_f64_to_f32(s, B.sv.X, (int64_t)p * p, B.X32));
-          TT_TRY(jacobi_block_f32(s, B.sv, B.X32, p, p, p, B.V32, p, 30));
-          TT_TRY((gemm<double, float, double>(s, p, p, p, 1.0, B.sv.X, 1, p, B.V32, 1, p, 0.0, B.W64, 1, p)));
-          TT_CUDA_CHECK(cudaMemcpyAsync(B.sv.X, B.W64, (size_t)p * p * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, s));
+          TT_TRY(jacobi_block_f32(s, B.sv, B.X32, p, p, p, nullptr, p, 30));
+          TT_TRY(convert_f32_to_f64(s, B.X32, (int64_t)p * p, B.sv.X));
           TT_TRY(read_back(s, B.sv.sweeps, &sweeps32, sizeof(int)));
           if (sweeps32 < 0) {
-            // the FP32 sweeps did not settle: finish the (nearly diagonalised) W = X V with
-            // FP64 one-sided Jacobi, which converges from there in a few sweeps
+            // the FP32 sweeps did not settle: finish the (nearly diagonalised) W with FP64
+            // one-sided Jacobi, which converges from there in a few sweeps
             TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<double>(p), 30, delta_scale));
             ++refined_bonds;
           }

@@ -44,8 +44,7 @@ inline Dims dims_of(const tt_train* x) {
 template <typename T>
 struct Bufs {
   T *A = nullptr, *Q = nullptr, *tmp = nullptr, *Rbuf = nullptr, *vsel = nullptr, *F = nullptr;
-  float *X32 = nullptr, *V32 = nullptr, *G32 = nullptr;  // mixed-form bond SVD
-  double* W64 = nullptr;
+  float *X32 = nullptr, *G32 = nullptr;  // mixed-form bond SVD: FP32 factor, Newton-Schulz Gram
   QrWork<T> qr;
   SvdWork sv;
 };
@@ -67,9 +66,7 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   B.sv.X = c.take<double>((size_t)D.r_max * D.r_max);
   if (std::is_same<T, float>::value) {
     B.X32 = c.take<float>((size_t)D.r_max * D.r_max);
-    B.V32 = c.take<float>((size_t)D.r_max * D.r_max);
     B.G32 = c.take<float>((size_t)D.r_max * D.r_max);
-    B.W64 = c.take<double>((size_t)D.r_max * D.r_max);
   }
   B.sv.sigma = c.take<double>(D.r_max);
   B.sv.perm = c.take<int>(D.r_max);

@@ -190,6 +190,123 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
   }
 }
 
+// The same FP64 Jacobi with one CTA of WPP warps per pair: the rows of the pair are split
+// over the warps (shorter dependent FMA chains, WPP times the warps per SM), the partial
+// sums are combined in shared memory in a fixed order, every warp derives the same
+// rotation and applies it to its rows.  Dataflow ordering between pairs as above.
+template <int WPP, int TPL>
+__global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nrow, int ncol, int ldx, double tol,
+                                                             double negl_scale, const double* norm, int max_sweeps,
+                                                             unsigned* bar, unsigned* rot, unsigned* status,
+                                                             int* sweeps_out, unsigned* epoch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double nl = negl_scale > 0.0 ? negl_scale * __ldcg(norm) : 0.0;
+  const double negl = nl * nl;
+  const int N = ncol + (ncol & 1), npairs = N / 2;
+  const int rows = (nrow + WPP - 1) / WPP;  // rows of one warp
+  const int i_lo = warp * rows, i_hi = min(nrow, i_lo + rows);
+  __shared__ double red[WPP][3];
+  __shared__ int s_ok;
+  int sweep = 0;
+  bool converged = false;
+  unsigned t = 0;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int rnd = 0; rnd < N - 1; ++rnd, ++t) {
+      for (int q = blockIdx.x; q < npairs; q += gridDim.x) {
+        int a, b;
+        if (q == 0) {
+          a = rnd;
+          b = N - 1;
+        } else {
+          a = (rnd + q) % (N - 1);
+          b = (rnd - q + N - 1) % (N - 1);
+        }
+        if (a > b) {
+          const int tmp = a;
+          a = b;
+          b = tmp;
+        }
+        const bool real_b = b < ncol;
+        if (threadIdx.x == 0) s_ok = wait_column(epoch, a, t, status) && (!real_b || wait_column(epoch, b, t, status));
+        __syncthreads();
+        if (!s_ok) {
+          // leave through the sweep barrier, which sees ST_TIMEOUT
+          q = npairs;
+          rnd = N;
+          break;
+        }
+        double* xa = X + (int64_t)a * ldx;
+        double* xb = X + (int64_t)b * ldx;
+        if (real_b) {
+          double ra[TPL], rb[TPL];
+          double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+          for (int u = 0; u < TPL; ++u) {
+            const int i = i_lo + lane + 32 * u;
+            ra[u] = i < i_hi ? __ldcg(xa + i) : 0.0;
+            rb[u] = i < i_hi ? __ldcg(xb + i) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < TPL; ++u) {
+            al = fma(ra[u], ra[u], al);
+            be = fma(rb[u], rb[u], be);
+            ga = fma(ra[u], rb[u], ga);
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          if (lane == 0) {
+            red[warp][0] = al;
+            red[warp][1] = be;
+            red[warp][2] = ga;
+          }
+          __syncthreads();
+          al = be = ga = 0.0;
+#pragma unroll
+          for (int w = 0; w < WPP; ++w) {
+            al += red[w][0];
+            be += red[w][1];
+            ga += red[w][2];
+          }
+          bool doit = !(al < negl && be < negl) && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be);
+          double c = 1.0, sn = 0.0;
+          if (doit) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double tn = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                                   : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + tn * tn);
+            sn = c * tn;
+            doit = sn != 0.0;
+          }
+          if (doit) {
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+              const int i = i_lo + lane + 32 * u;
+              if (i < i_hi) {
+                __stcg(xa + i, c * ra[u] - sn * rb[u]);
+                __stcg(xb + i, sn * ra[u] + c * rb[u]);
+              }
+            }
+            if (threadIdx.x == 0) atomicAdd(rot + sweep, 1u);
+          }
+        }
+        __syncthreads();  // every warp's stores (and reads of red) precede the release
+        if (threadIdx.x == 0) {
+          __threadfence();
+          st_release_u32(epoch + a, t + 1);
+          if (real_b) st_release_u32(epoch + b, t + 1);
+        }
+      }
+    }
+    if (!sweep_barrier(bar, status)) return;
+    converged = (*(volatile unsigned*)(rot + sweep) == 0u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *sweeps_out = sweep;
+    if (!converged) atomicOr(status, (unsigned)ST_NONCONVERGED);
+  }
+}
+
 // FP32 one-sided Jacobi with accumulated rotations, organised as a block round-robin:
 // the columns are cut into groups of 16; in each outer round a CTA takes one pair of
 // groups (32 columns of X and of V) into shared memory and sweeps all pairs among
@@ -356,7 +473,7 @@ __global__ void __launch_bounds__(32 * GS) jacobi_block_f32_kernel(float* X, int
         if (tid == 0) s_rot = 0;
         __syncthreads();
         load_cols<8>(Xs, X, cols, C2, nrow, ldx);
-        load_cols<8>(Vs, V, cols, C2, ncol, ldv);
+        if (V) load_cols<8>(Vs, V, cols, C2, ncol, ldv);
         __syncthreads();
         // inner round-robin over the 2 GS local slots: 2 GS - 1 rounds x GS pairs
         unsigned local = 0;
@@ -371,13 +488,13 @@ __global__ void __launch_bounds__(32 * GS) jacobi_block_f32_kernel(float* X, int
           }
           if (cols[a] >= 0 && cols[b] >= 0 &&
               rotate_pair_f32<TPL>(Xs + (size_t)a * nrow, Xs + (size_t)b * nrow, Vs + (size_t)a * ncol,
-                                   Vs + (size_t)b * ncol, nrow, ncol, lane, tol, negl))
+                                   Vs + (size_t)b * ncol, nrow, V ? ncol : 0, lane, tol, negl))
             ++local;
           __syncthreads();
         }
         if (lane == 0 && local) atomicAdd(&s_rot, local);
         store_cols(Xs, X, cols, C2, nrow, ldx);
-        store_cols(Vs, V, cols, C2, ncol, ldv);
+        if (V) store_cols(Vs, V, cols, C2, ncol, ldv);
         __syncthreads();
         if (tid == 0 && s_rot) atomicAdd(rot + sweep, s_rot);
         if (flow && tid == 0) {
@@ -773,6 +890,42 @@ __global__ void svd_left_batched_kernel(const SvdJob* __restrict__ jobs) {
 
 }  // namespace
 
+template <int TPL>
+int launch_wpp(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, double negl_scale, int max_sweeps) {
+  constexpr int WPP = 4, NT = 32 * WPP;
+  static int cfg_dev = -1, cfg_blocks = 0;
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  if (cfg_dev != dev) {
+    int occ = 0;
+    TT_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_wpp_kernel<WPP, TPL>, NT, 0));
+    cfg_blocks = occ * num_sms();
+    cfg_dev = dev;
+  }
+  const int npairs = (ncol + 1) / 2;
+  int blocks = std::min(npairs, cfg_blocks);
+  if (blocks < 1) blocks = 1;
+  TT_CUDA_CHECK(cudaMemsetAsync(w.epoch, 0, (size_t)ncol * sizeof(unsigned), s));
+  double* X = w.X;
+  int ldx = w.ldx;
+  const double* nrm = w.norm;
+  unsigned *bar = w.bar, *rot = w.rot, *st = w.status, *ep = w.epoch;
+  int* sw = w.sweeps;
+  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &negl_scale, &nrm, &max_sweeps, &bar, &rot, &st, &sw, &ep};
+  TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_wpp_kernel<WPP, TPL>, dim3(blocks), dim3(NT), args,
+                                            0, s));
+  note_launch();
+  return TT_OK;
+}
+
+int launch_jacobi_wpp(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, double negl_scale,
+                      int max_sweeps) {
+  // rows per warp = nrow / 4, in registers: 32 TPL >= that
+  if (nrow <= 128) return launch_wpp<1>(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
+  if (nrow <= 256) return launch_wpp<2>(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
+  return launch_wpp<4>(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
+}
+
 template <int NT, int TPL>
 int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, double negl_scale,
                   int max_sweeps) {
@@ -783,7 +936,9 @@ int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, do
     TT_LAUNCH_CHECK();
     return TT_OK;
   }
-  // the dataflow ordering needs one epoch counter per column (SvdWork::epoch)
+  // the dataflow ordering needs one epoch counter per column (SvdWork::epoch); with it,
+  // one CTA of four warps per pair (rows split) when each warp gets at most 128 rows
+  if (w.epoch != nullptr && nrow <= 512) return launch_jacobi_wpp(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
   const bool flow = w.epoch != nullptr;
   const void* fn = flow ? (const void*)jacobi_kernel<NT, TPL, true> : (const void*)jacobi_kernel<NT, TPL, false>;
   static int cfg_dev = -1, cfg_blocks = 0;
@@ -889,9 +1044,11 @@ int launch_jacobi_block(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol
     cfg_blocks = std::max(1, occ) * num_sms();
     cfg_dev = dev;
   }
-  identity_f32_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)ncol * ncol, 256), 4096), 256, 0, s>>>(
-      V, ncol, ldv);
-  TT_LAUNCH_CHECK();
+  if (V) {
+    identity_f32_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)ncol * ncol, 256), 4096), 256, 0, s>>>(
+        V, ncol, ldv);
+    TT_LAUNCH_CHECK();
+  }
   TT_CUDA_CHECK(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
   TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
   const int G = (ncol + GS - 1) / GS;

@@ -26,8 +26,8 @@ struct SvdWork {
 int jacobi_svd(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, int max_sweeps,
                double delta_scale = 0.0);
 
-// FP32 one-sided Jacobi with accumulated rotations (V = I on entry is set here), block
-// round-robin in shared memory; the fast part of the mixed form's bond SVD.  *w.sweeps
+// FP32 one-sided Jacobi, block round-robin in shared memory; the rotations are accumulated
+// in V (V = I on entry is set here) unless V is null.  *w.sweeps
 // receives the sweep count, or -1 if max_sweeps passed without convergence (no status
 // flag is raised: the caller finishes the SVD in FP64 then).
 size_t jacobi_block_smem(int nrow, int ncol);
@@ -50,8 +50,7 @@ int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ld
 struct SvdJob {
   double* X;        // n x n FP64 factor, column-major, ld ldx (rotated in place / W)
   int n, ldx;
-  float* X32;       // mixed form: FP32 copy of the factor and the accumulated rotations
-  float* V32;
+  float* X32;       // mixed form: FP32 copy of the factor, rotated in place
   int ld32;
   double* sigma;
   int* perm;
