@@ -120,10 +120,6 @@ struct TrainState {
   Bufs<T> B;
 };
 
-template <typename T>
-int64_t tiles64(int64_t M, int64_t N) {
-  return ceil_div(M, 64) * ceil_div(N, 64);
-}
 
 template <typename T>
 MapJob copy_job(const T* src, T* dst, int64_t n) {
@@ -229,6 +225,15 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     TT_CUDA_CHECK(cudaStreamSynchronize(s));
     return TT_OK;
   };
+  // one dense batched GEMM launch: host jobs (for the tile prefix), their device copy
+  auto dense_gemm = [&](const auto& hv, const auto* dv) -> int {
+    if (hv.empty()) return TT_OK;
+    std::vector<int> pre(hv.size() + 1);
+    const TilePlan plan = tile_prefix(hv.data(), (int)hv.size(), pre.data());
+    const int* dp = arena.push(pre, s);
+    if (!dp) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
+    return gemm_batched_dense(s, (int)hv.size(), dv, dp, plan);
+  };
   auto step_end = [&]() -> int {
     TT_CUDA_CHECK(cudaStreamSynchronize(s));
     arena.reset();
@@ -264,8 +269,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     std::vector<MapJob> cin, rext, cout_;
     std::vector<QrJob<T>> qj;
     std::vector<GemmJob<T, T, T>> gj;
-    int64_t mx_in = 0, mx_r = 0, mx_out = 0, t64 = 0;
-    int gm = 0, gn = 0;
+    int64_t mx_in = 0, mx_r = 0, mx_out = 0;
     for (int i : act) {
       TrainState<T>& S = tr[i];
       const int k = S.L - 1 - step;
@@ -279,9 +283,6 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
       mx_r = std::max<int64_t>(mx_r, (int64_t)pp * nn);
       const int rows = (int)S.cur[k - 1] * S.d[k - 1];
       gj.push_back(GemmJob<T, T, T>{S.slot[k - 1], B.Rbuf, B.tmp, nn, 1, pp, 1, pp, 1, rows, pp, nn, 1.0, 0.0});
-      t64 += tiles64<T>(rows, pp);
-      gm = std::max(gm, rows);
-      gn = std::max(gn, pp);
       cout_.push_back(copy_job<T>(B.tmp, S.slot[k - 1], (int64_t)rows * pp));
       mx_out = std::max<int64_t>(mx_out, (int64_t)rows * pp);
     }
@@ -297,7 +298,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     TT_TRY(householder_qr_batched<T>(s, qj, d_qj, nb, arena));
     TT_TRY(form_thin_q_batched<T>(s, qj, d_qj, nb, arena));
     TT_TRY((map_batched<T, T>(s, na, d_rext, mx_r)));
-    TT_TRY((gemm_batched<T, T, T>(s, na, d_gj, gm, gn, t64)));
+    TT_TRY(dense_gemm(gj, d_gj));
     TT_TRY((map_batched<T, T>(s, na, d_cout, mx_out)));
     for (int i : act) {
       TrainState<T>& S = tr[i];
@@ -532,8 +533,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
         // one Newton-Schulz step U <- U (3I - U^T U) / 2 (as in tt_round)
         std::vector<GemmJob<float, float, float>> g1, g2;
         std::vector<MapJob> h, cpy;
-        int64_t t1 = 0, t2 = 0, mx_g = 0;
-        int m1 = 0, m2 = 0;
+        int64_t mx_g = 0, mx_h = 0;
         for (int a : svd_a) {
           Bufs<T>& B = tr[act[a]].B;
           const int q = pp_[a], r = rn[a];
@@ -542,20 +542,17 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
           h.push_back(MapJob{B.G32, B.G32, r, r, 1, r, 1, r, MAP_NS});
           g2.push_back(GemmJob<float, float, float>{U, B.G32, B.X32, 1, q, 1, r, 1, q, q, r, r, 1.0, 0.0});
           cpy.push_back(copy_job<float>(B.X32, U, (int64_t)q * r));
-          t1 += tiles64<T>(r, r);
-          t2 += tiles64<T>(q, r);
-          m1 = std::max(m1, r);
-          m2 = std::max(m2, q);
           mx_g = std::max<int64_t>(mx_g, (int64_t)q * r);
+          mx_h = std::max<int64_t>(mx_h, (int64_t)r * r);
         }
         const GemmJob<float, float, float>* d_g1 = arena.push(g1, s);
         const MapJob* d_h = arena.push(h, s);
         const GemmJob<float, float, float>* d_g2 = arena.push(g2, s);
         const MapJob* d_cpy = arena.push(cpy, s);
         if (!d_g1 || !d_h || !d_g2 || !d_cpy) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
-        TT_TRY((gemm_batched<float, float, float>(s, ns, d_g1, m1, m1, t1)));
-        TT_TRY((map_batched<float, float>(s, ns, d_h, (int64_t)m1 * m1)));
-        TT_TRY((gemm_batched<float, float, float>(s, ns, d_g2, m2, m1, t2)));
+        TT_TRY(dense_gemm(g1, d_g1));
+        TT_TRY((map_batched<float, float>(s, ns, d_h, mx_h)));
+        TT_TRY(dense_gemm(g2, d_g2));
         TT_TRY((map_batched<float, float>(s, ns, d_cpy, mx_g)));
       }
     }
@@ -563,8 +560,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     // ---- new cores: C_k and the factor F that multiplies C_{k+1}
     std::vector<GemmJob<T, T, T>> ga, gb, gc;
     std::vector<MapJob> ma, mc;
-    int64_t ta = 0, tb = 0, tc = 0, mx_a = 0, mx_c = 0;
-    int am = 0, an = 0, bm = 0, bn = 0, cm = 0, cn = 0;
+    int64_t mx_a = 0, mx_c = 0;
     for (int a = 0; a < na; ++a) {
       TrainState<T>& S = tr[act[a]];
       Bufs<T>& B = S.B;
@@ -578,27 +574,15 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
       } else if (tall[a]) {
         // C_k <- Q U_r (m x r row-major); F = U_r^T R (r x nn row-major)
         ga.push_back(GemmJob<T, T, T>{B.Q, B.vsel, S.slot[k], 1, m, 1, q, r, 1, m, r, q, 1.0, 0.0});
-        ta += tiles64<T>(m, r);
-        am = std::max(am, m);
-        an = std::max(an, r);
         gb.push_back(GemmJob<T, T, T>{B.vsel, B.Rbuf, B.F, q, 1, 1, q, nn, 1, r, nn, q, 1.0, 0.0});
-        tb += tiles64<T>(r, nn);
-        bm = std::max(bm, r);
-        bn = std::max(bn, nn);
         gc.push_back(GemmJob<T, T, T>{B.F, S.slot[k + 1], B.tmp, nn, 1, cols, 1, cols, 1, r, cols, nn, 1.0, 0.0});
       } else {
         // F = U_r^T C_k (r x nn from the original core), then C_k <- U_r (row-major m x r)
         gb.push_back(GemmJob<T, T, T>{B.vsel, S.slot[k], B.F, m, 1, nn, 1, nn, 1, r, nn, m, 1.0, 0.0});
-        tb += tiles64<T>(r, nn);
-        bm = std::max(bm, r);
-        bn = std::max(bn, nn);
         ma.push_back(MapJob{B.vsel, S.slot[k], m, r, 1, m, r, 1, MAP_COPY});
         mx_a = std::max<int64_t>(mx_a, (int64_t)m * r);
         gc.push_back(GemmJob<T, T, T>{B.F, S.slot[k + 1], B.tmp, nn, 1, cols, 1, cols, 1, r, cols, nn, 1.0, 0.0});
       }
-      tc += tiles64<T>(r, cols);
-      cm = std::max(cm, r);
-      cn = std::max(cn, cols);
       mc.push_back(copy_job<T>(B.tmp, S.slot[k + 1], (int64_t)r * cols));
       mx_c = std::max<int64_t>(mx_c, (int64_t)r * cols);
     }
@@ -610,10 +594,10 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     const MapJob* d_ma = arena.push(ma, s);
     const MapJob* d_mc = arena.push(mc, s);
     if (!d_ga || !d_gb || !d_gc || !d_ma || !d_mc) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
-    if (!gb.empty()) TT_TRY((gemm_batched<T, T, T>(s, (int)gb.size(), d_gb, bm, bn, tb)));
-    if (!ga.empty()) TT_TRY((gemm_batched<T, T, T>(s, (int)ga.size(), d_ga, am, an, ta)));
+    TT_TRY(dense_gemm(gb, d_gb));
+    TT_TRY(dense_gemm(ga, d_ga));
     if (!ma.empty()) TT_TRY((map_batched<T, T>(s, (int)ma.size(), d_ma, mx_a)));
-    TT_TRY((gemm_batched<T, T, T>(s, na, d_gc, cm, cn, tc)));
+    TT_TRY(dense_gemm(gc, d_gc));
     TT_TRY((map_batched<T, T>(s, na, d_mc, mx_c)));
     for (int a = 0; a < na; ++a) tr[act[a]].cur[k + 1] = rn[a];
     TT_TRY(step_end());

@@ -150,6 +150,26 @@ __global__ void __launch_bounds__(NT) gemm_batched_kernel(const GemmJob<TA, TB, 
                                       j.scm, j.scn, blockIdx.x, blockIdx.y);
 }
 
+// Dense batched form: one CTA per real tile.  prefix[j] = tiles of jobs 0..j-1 (njobs + 1
+// entries); a CTA finds its job by binary search and its tile from the remainder, so no
+// CTA is spent on the empty tiles of a grid sized for the largest job.
+template <int BM, int BN, typename TA, typename TB, typename TC, bool COMP>
+__global__ void __launch_bounds__(NT) gemm_dense_kernel(const GemmJob<TA, TB, TC>* __restrict__ jobs,
+                                                        const int* __restrict__ prefix, int njobs) {
+  const int id = blockIdx.x;
+  int lo = 0, hi = njobs;  // last job with prefix[job] <= id
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= id) lo = mid;
+    else hi = mid;
+  }
+  const GemmJob<TA, TB, TC> j = jobs[lo];
+  const int local = id - prefix[lo];
+  const int tn = (j.N + BN - 1) / BN;
+  gemm_tile<BM, BN, TA, TB, TC, COMP>(j.M, j.N, j.K, j.alpha, j.A, j.sam, j.sak, j.B, j.sbk, j.sbn, j.beta, j.C,
+                                      j.scm, j.scn, local % tn, local / tn);
+}
+
 template <typename TC>
 __global__ void scale_kernel(int M, int N, double beta, TC* C, int64_t scm, int64_t scn) {
   const int64_t total = (int64_t)M * N;
@@ -220,11 +240,49 @@ int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, i
   return TT_OK;
 }
 
+template <typename TA, typename TB, typename TC>
+TilePlan tile_prefix(const GemmJob<TA, TB, TC>* jobs, int njobs, int* prefix) {
+  TilePlan plan;
+  int64_t t64 = 0;
+  for (int i = 0; i < njobs; ++i)
+    if (jobs[i].M > 0 && jobs[i].N > 0 && jobs[i].K > 0) t64 += ceil_div(jobs[i].M, 64) * ceil_div(jobs[i].N, 64);
+  plan.tile = t64 >= num_sms() ? 64 : 32;
+  int64_t acc = 0;
+  for (int i = 0; i < njobs; ++i) {
+    prefix[i] = (int)acc;
+    if (jobs[i].M > 0 && jobs[i].N > 0 && jobs[i].K > 0)
+      acc += ceil_div(jobs[i].M, plan.tile) * ceil_div(jobs[i].N, plan.tile);
+  }
+  prefix[njobs] = (int)acc;
+  plan.total = acc;
+  return plan;
+}
+
+template <typename TA, typename TB, typename TC>
+int gemm_batched_dense(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, const int* d_prefix,
+                       const TilePlan& plan, bool compensated) {
+  if (njobs <= 0 || plan.total <= 0) return TT_OK;
+  if (plan.total > 0x7fffffff) return fail(TT_ERR_UNSUPPORTED, "gemm_batched_dense: too many tiles");
+  const unsigned g = (unsigned)plan.total;
+  if (plan.tile == 64) {
+    if (compensated) gemm_dense_kernel<64, 64, TA, TB, TC, true><<<g, NT, 0, s>>>(d_jobs, d_prefix, njobs);
+    else gemm_dense_kernel<64, 64, TA, TB, TC, false><<<g, NT, 0, s>>>(d_jobs, d_prefix, njobs);
+  } else {
+    if (compensated) gemm_dense_kernel<32, 32, TA, TB, TC, true><<<g, NT, 0, s>>>(d_jobs, d_prefix, njobs);
+    else gemm_dense_kernel<32, 32, TA, TB, TC, false><<<g, NT, 0, s>>>(d_jobs, d_prefix, njobs);
+  }
+  TT_LAUNCH_CHECK();
+  return TT_OK;
+}
+
 #define TT_GEMM_INST(TA, TB, TC)                                                           \
   template int gemm<TA, TB, TC>(cudaStream_t, int, int, int, double, const TA*, int64_t, \
                                 int64_t, const TB*, int64_t, int64_t, double, TC*, int64_t, \
                                 int64_t);                                                  \
-  template int gemm_batched<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, int, int, int64_t, bool);
+  template int gemm_batched<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, int, int, int64_t, bool); \
+  template TilePlan tile_prefix<TA, TB, TC>(const GemmJob<TA, TB, TC>*, int, int*);                            \
+  template int gemm_batched_dense<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, const int*,       \
+                                              const TilePlan&, bool);
 TT_GEMM_INST(double, double, double)
 TT_GEMM_INST(double, double, float)
 TT_GEMM_INST(double, float, double)

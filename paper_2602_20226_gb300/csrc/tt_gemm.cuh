@@ -32,6 +32,19 @@ template <typename TA, typename TB, typename TC>
 int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, int M_max, int N_max,
                  int64_t tiles64, bool compensated = true);
 
+// Dense batched form: prefix (njobs + 1 host ints) = running tile counts for the tile size
+// the plan picks (64 x 64 when they give at least one CTA per SM, else 32 x 32); the same
+// array in device memory goes to gemm_batched_dense, which launches one CTA per real tile.
+struct TilePlan {
+  int tile = 64;
+  int64_t total = 0;
+};
+template <typename TA, typename TB, typename TC>
+TilePlan tile_prefix(const GemmJob<TA, TB, TC>* jobs, int njobs, int* prefix);
+template <typename TA, typename TB, typename TC>
+int gemm_batched_dense(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, const int* d_prefix,
+                       const TilePlan& plan, bool compensated = true);
+
 // FP32 GEMM on the tensor cores, TF32 with a 3-term hi/lo split (tt_gemm_tc.cu).
 // acc64: sum the per-K-block tensor-core partials in FP64 registers.
 int gemm_tf32x3(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,

@@ -505,6 +505,7 @@ struct PanelGemms {
   std::vector<GemmJob<T, T, T>> w1, w2, up;
   int64_t t1 = 0, t2 = 0, t3 = 0;
   int m1 = 0, n1 = 0, m3 = 0;
+  TilePlan p1, p2, p3;  // dense tile plans of the three GEMMs
 };
 
 template <typename T>
@@ -556,40 +557,58 @@ void panel_gemm_jobs(const QrJob<T>& J, int j0, int nb, bool formq, PanelGemms<T
 // the error of 20..60-site trains at eps = 1e-6 from ~2e-6 to 4.6e-6.  FP64: W2 by the
 // reflector kernel (one CTA per column), then the update GEMM - measured faster in FP64,
 // where the work is bound by the FP64 pipe rather than by L2 traffic.
+// d1..d3: the GEMM jobs of every panel ([panel][job]); e1..e3: their tile prefixes
+// ([panel][job + 1]).
 template <typename T>
 int apply_panels(cudaStream_t s, const QrJob<T>* d_jobs, int nj, int nb, bool formq, int pn,
                  const GemmJob<T, T, T>* d1, const GemmJob<T, T, T>* d2, const GemmJob<T, T, T>* d3,
-                 const std::vector<PanelGemms<T>>& meta) {
+                 const int* e1, const int* e2, const int* e3, const std::vector<PanelGemms<T>>& meta) {
   const PanelGemms<T>& M = meta[pn];
   if (M.n1 <= 0) return TT_OK;
+  const size_t jo = (size_t)pn * nj, po = (size_t)pn * (nj + 1);
   if (sizeof(T) == 4) {
-    TT_TRY((gemm_batched<T, T, T>(s, nj, d1 + (size_t)pn * nj, M.m1, M.n1, M.t1)));
-    TT_TRY((gemm_batched<T, T, T>(s, nj, d2 + (size_t)pn * nj, M.m1, M.n1, M.t2)));
+    TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d1 + jo, e1 + po, M.p1)));
+    TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d2 + jo, e2 + po, M.p2)));
   } else {
     reflector_w_batched_kernel<T, 256><<<dim3((unsigned)M.n1, (unsigned)nj), 256, 0, s>>>(d_jobs, pn * nb, nb,
                                                                                           formq);
     TT_LAUNCH_CHECK();
   }
-  TT_TRY((gemm_batched<T, T, T>(s, nj, d3 + (size_t)pn * nj, M.m3, M.n1, M.t3)));
+  TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d3 + jo, e3 + po, M.p3)));
   return TT_OK;
 }
 
 template <typename T>
+struct PanelArrays {
+  const GemmJob<T, T, T> *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;
+  const int *e1 = nullptr, *e2 = nullptr, *e3 = nullptr;
+};
+
+template <typename T>
 int build_panel_gemms(cudaStream_t s, const std::vector<QrJob<T>>& hj, int nb, bool formq, int npanels,
-                      JobArena& arena, std::vector<PanelGemms<T>>& meta, const GemmJob<T, T, T>** d1,
-                      const GemmJob<T, T, T>** d2, const GemmJob<T, T, T>** d3) {
+                      JobArena& arena, std::vector<PanelGemms<T>>& meta, PanelArrays<T>& D) {
+  const int nj = (int)hj.size();
   meta.assign(npanels, PanelGemms<T>{});
   std::vector<GemmJob<T, T, T>> a1, a2, a3;
+  std::vector<int> q1((size_t)npanels * (nj + 1)), q2(q1.size()), q3(q1.size());
   for (int pn = 0; pn < npanels; ++pn) {
-    for (const auto& J : hj) panel_gemm_jobs(J, pn * nb, nb, formq, meta[pn]);
-    a1.insert(a1.end(), meta[pn].w1.begin(), meta[pn].w1.end());
-    a2.insert(a2.end(), meta[pn].w2.begin(), meta[pn].w2.end());
-    a3.insert(a3.end(), meta[pn].up.begin(), meta[pn].up.end());
+    PanelGemms<T>& M = meta[pn];
+    for (const auto& J : hj) panel_gemm_jobs(J, pn * nb, nb, formq, M);
+    const size_t po = (size_t)pn * (nj + 1);
+    M.p1 = tile_prefix(M.w1.data(), nj, q1.data() + po);
+    M.p2 = tile_prefix(M.w2.data(), nj, q2.data() + po);
+    M.p3 = tile_prefix(M.up.data(), nj, q3.data() + po);
+    a1.insert(a1.end(), M.w1.begin(), M.w1.end());
+    a2.insert(a2.end(), M.w2.begin(), M.w2.end());
+    a3.insert(a3.end(), M.up.begin(), M.up.end());
   }
-  *d1 = arena.push(a1, s);
-  *d2 = arena.push(a2, s);
-  *d3 = arena.push(a3, s);
-  if (!*d1 || !*d2 || !*d3) return fail(TT_ERR_WORKSPACE, "batched QR: job arena full");
+  D.d1 = arena.push(a1, s);
+  D.d2 = arena.push(a2, s);
+  D.d3 = arena.push(a3, s);
+  D.e1 = arena.push(q1, s);
+  D.e2 = arena.push(q2, s);
+  D.e3 = arena.push(q3, s);
+  if (!D.d1 || !D.d2 || !D.d3 || !D.e1 || !D.e2 || !D.e3) return fail(TT_ERR_WORKSPACE, "batched QR: job arena full");
   return TT_OK;
 }
 
@@ -614,14 +633,14 @@ int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, cons
   }
   const int npanels = (int)ceil_div(p_max, nb);
   std::vector<PanelGemms<T>> meta;
-  const GemmJob<T, T, T> *d1, *d2, *d3;
-  TT_TRY(build_panel_gemms(s, hj, nb, false, npanels, arena, meta, &d1, &d2, &d3));
+  PanelArrays<T> D;
+  TT_TRY(build_panel_gemms(s, hj, nb, false, npanels, arena, meta, D));
   for (int pn = 0; pn < npanels; ++pn) {
     const int j0 = pn * nb;
     const size_t smem = std::min(kPanelSmem, (size_t)(m_max - j0) * nb * sizeof(T));
     qr_panel_batched_kernel<T, 512><<<nj, 512, smem, s>>>(d_jobs, j0, nb, smem);
     TT_LAUNCH_CHECK();
-    TT_TRY(apply_panels(s, d_jobs, nj, nb, false, pn, d1, d2, d3, meta));
+    TT_TRY(apply_panels(s, d_jobs, nj, nb, false, pn, D.d1, D.d2, D.d3, D.e1, D.e2, D.e3, meta));
   }
   return TT_OK;
 }
@@ -643,9 +662,10 @@ int form_thin_q_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const Q
   TT_LAUNCH_CHECK();
   const int npanels = (int)ceil_div(p_max, nb);
   std::vector<PanelGemms<T>> meta;
-  const GemmJob<T, T, T> *d1, *d2, *d3;
-  TT_TRY(build_panel_gemms(s, hj, nb, true, npanels, arena, meta, &d1, &d2, &d3));
-  for (int pn = npanels - 1; pn >= 0; --pn) TT_TRY(apply_panels(s, d_jobs, nj, nb, true, pn, d1, d2, d3, meta));
+  PanelArrays<T> D;
+  TT_TRY(build_panel_gemms(s, hj, nb, true, npanels, arena, meta, D));
+  for (int pn = npanels - 1; pn >= 0; --pn)
+    TT_TRY(apply_panels(s, d_jobs, nj, nb, true, pn, D.d1, D.d2, D.d3, D.e1, D.e2, D.e3, meta));
   return TT_OK;
 }
 
