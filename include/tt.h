@@ -237,15 +237,31 @@ void tt_profile_enable(int32_t on);
 int tt_profile_read(int32_t cls, double* ms, double* nominal_flops, uint64_t* count);
 
 /* C = alpha A B + beta C in FP32 on the tensor cores: TF32 with a 3-term hi/lo split
- * (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation), the dense-GEMM kernel the
- * mixed form of tt_round uses.  No counterpart in the paper; exported so that the
- * tensor-core kernel can be tested and timed on its own.
+ * (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation).  Not on the rounding path: the
+ * tensor cores round each accumulation toward zero, a bias the mixed form cannot afford
+ * (tt_gemm_f32_sliced is the form it uses).  No counterpart in the paper.
  * Element (m, k) of A is A[m*sam + k*sak], (k, n) of B is B[k*sbk + n*sbn], (m, n) of
  * C is C[m*scm + n*scn] (device pointers; any strides).  beta = 0 never reads C.
  * Asynchronous. */
 int tt_gemm_f32(int32_t M, int32_t N, int32_t K, double alpha, const float* A, int64_t sam,
                 int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
                 int64_t scm, int64_t scn, void* stream);
+
+/* C = alpha A B + beta C in FP32 on the tensor cores in the sliced form, the GEMM of the
+ * mixed form of tt_round and tt_apply_round_batched (K >= 16).  Per 16-wide block of K,
+ * each row of A and each column of B is scaled by its own power of two and cut into
+ * three signed integer slices rounded to nearest (h1 + 2^-9 h2 + 2^-18 h3, |h1| <= 512,
+ * |h2|, |h3| <= 256); six TF32 tcgen05 MMAs per K step form three level sums of slice
+ * products, integers below 2^23 and therefore exact whatever the tensor core's rounding;
+ * the levels are scaled and added in float-float.  Error per element <= 2^-21 sum over
+ * 16-wide K blocks of max|a| max|b| (the dropped h2 h3, h3 h2, h3 h3 terms and the last
+ * slice's rounding; zero-mean), plus the final rounding to FP32.  Rows or
+ * columns whose block maximum is below 2^-118 count as zero in that block.  No
+ * counterpart in the paper (Ozaki-type splitting).  Arguments as tt_gemm_f32; K = 0
+ * scales C by beta.  Asynchronous. */
+int tt_gemm_f32_sliced(int32_t M, int32_t N, int32_t K, double alpha, const float* A, int64_t sam,
+                       int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
+                       int64_t scm, int64_t scn, void* stream);
 
 #ifdef __cplusplus
 }

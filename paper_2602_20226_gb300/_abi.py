@@ -72,6 +72,7 @@ SIGNATURES = {
     "tt_apply_round_batched": (ctypes.c_int, [i32, P(tt_mpo), P(tt_train), P(tt_train), f64, i64, i32,
                                               P(tt_train), vp, sz, P(vp), i32]),
     "tt_gemm_f32": (ctypes.c_int, [i32, i32, i32, f64, vp, i64, i64, vp, i64, i64, f64, vp, i64, i64, vp]),
+    "tt_gemm_f32_sliced": (ctypes.c_int, [i32, i32, i32, f64, vp, i64, i64, vp, i64, i64, f64, vp, i64, i64, vp]),
 }
 
 _lib = None

@@ -489,4 +489,16 @@ int tt_gemm_f32(int32_t M, int32_t N, int32_t K, double alpha, const float* A, i
   });
 }
 
+int tt_gemm_f32_sliced(int32_t M, int32_t N, int32_t K, double alpha, const float* A, int64_t sam,
+                       int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
+                       int64_t scm, int64_t scn, void* stream) {
+  return guarded([&]() -> int {
+    if (M < 0 || N < 0 || K < 0) return fail(TT_ERR_ARG, "tt_gemm_f32_sliced: negative size");
+    if ((M > 0 && N > 0) && (!C || (K > 0 && (!A || !B))))
+      return fail(TT_ERR_ARG, "tt_gemm_f32_sliced: NULL operand");
+    g_last_error.clear();
+    return gemm_sliced(as_stream(stream), M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, nullptr);
+  });
+}
+
 }  // extern "C"

@@ -232,7 +232,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     const TilePlan plan = tile_prefix(hv.data(), (int)hv.size(), pre.data());
     const int* dp = arena.push(pre, s);
     if (!dp) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
-    return gemm_batched_dense(s, (int)hv.size(), dv, dp, plan);
+    return gemm_batched_dense(s, (int)hv.size(), dv, dp, plan, true, R.status);  // timeouts: train 0's word
   };
   auto step_end = [&]() -> int {
     TT_CUDA_CHECK(cudaStreamSynchronize(s));
@@ -295,8 +295,8 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     if (!d_cin || !d_qj || !d_rext || !d_gj || !d_cout)
       return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
     TT_TRY((map_batched<T, T>(s, na, d_cin, mx_in)));
-    TT_TRY(householder_qr_batched<T>(s, qj, d_qj, nb, arena));
-    TT_TRY(form_thin_q_batched<T>(s, qj, d_qj, nb, arena));
+    TT_TRY(householder_qr_batched<T>(s, qj, d_qj, nb, arena, R.status));
+    TT_TRY(form_thin_q_batched<T>(s, qj, d_qj, nb, arena, R.status));
     TT_TRY((map_batched<T, T>(s, na, d_rext, mx_r)));
     TT_TRY(dense_gemm(gj, d_gj));
     TT_TRY((map_batched<T, T>(s, na, d_cout, mx_out)));
@@ -369,10 +369,10 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
       return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
     TT_TRY((map_batched<T, T>(s, na, d_cin, mx_in)));
     if (!qj_tall.empty()) {
-      TT_TRY(householder_qr_batched<T>(s, qj_tall, d_qt, nb, arena));
-      TT_TRY(form_thin_q_batched<T>(s, qj_tall, d_qt, nb, arena));
+      TT_TRY(householder_qr_batched<T>(s, qj_tall, d_qt, nb, arena, R.status));
+      TT_TRY(form_thin_q_batched<T>(s, qj_tall, d_qt, nb, arena, R.status));
     }
-    if (!qj_wide.empty()) TT_TRY(householder_qr_batched<T>(s, qj_wide, d_qw, nb, arena));
+    if (!qj_wide.empty()) TT_TRY(householder_qr_batched<T>(s, qj_wide, d_qw, nb, arena, R.status));
     TT_TRY((map_batched<T, T>(s, na, d_rext, mx_r)));
     TT_TRY((map_batched<T, double>(s, na, d_xext, mx_x)));
     tm.mark(2);

@@ -243,6 +243,24 @@ int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, i
 template <typename TA, typename TB, typename TC>
 TilePlan tile_prefix(const GemmJob<TA, TB, TC>* jobs, int njobs, int* prefix) {
   TilePlan plan;
+  if constexpr (std::is_same_v<TA, float> && std::is_same_v<TB, float> && std::is_same_v<TC, float>) {
+    // the sliced tensor-core form when its 128 x 64 tiles give every SM a CTA; below that
+    // the SIMT tiles, up to 8x more CTAs, finish first
+    int64_t sl = 0;
+    for (int i = 0; i < njobs; ++i)
+      if (jobs[i].K > 0) sl += sliced_tiles(jobs[i].M, jobs[i].N);
+    if (sl >= num_sms()) {
+      plan.tile = kSlicedPlan;
+      int64_t acc = 0;
+      for (int i = 0; i < njobs; ++i) {
+        prefix[i] = (int)acc;
+        if (jobs[i].K > 0) acc += sliced_tiles(jobs[i].M, jobs[i].N);
+      }
+      prefix[njobs] = (int)acc;
+      plan.total = acc;
+      return plan;
+    }
+  }
   int64_t t64 = 0;
   for (int i = 0; i < njobs; ++i)
     if (jobs[i].M > 0 && jobs[i].N > 0 && jobs[i].K > 0) t64 += ceil_div(jobs[i].M, 64) * ceil_div(jobs[i].N, 64);
@@ -260,8 +278,11 @@ TilePlan tile_prefix(const GemmJob<TA, TB, TC>* jobs, int njobs, int* prefix) {
 
 template <typename TA, typename TB, typename TC>
 int gemm_batched_dense(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, const int* d_prefix,
-                       const TilePlan& plan, bool compensated) {
+                       const TilePlan& plan, bool compensated, unsigned* status) {
   if (njobs <= 0 || plan.total <= 0) return TT_OK;
+  if constexpr (std::is_same_v<TA, float> && std::is_same_v<TB, float> && std::is_same_v<TC, float>) {
+    if (plan.tile == kSlicedPlan) return gemm_sliced_dense(s, njobs, d_jobs, d_prefix, plan.total, status);
+  }
   if (plan.total > 0x7fffffff) return fail(TT_ERR_UNSUPPORTED, "gemm_batched_dense: too many tiles");
   const unsigned g = (unsigned)plan.total;
   if (plan.tile == 64) {
@@ -282,7 +303,7 @@ int gemm_batched_dense(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_j
   template int gemm_batched<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, int, int, int64_t, bool); \
   template TilePlan tile_prefix<TA, TB, TC>(const GemmJob<TA, TB, TC>*, int, int*);                            \
   template int gemm_batched_dense<TA, TB, TC>(cudaStream_t, int, const GemmJob<TA, TB, TC>*, const int*,       \
-                                              const TilePlan&, bool);
+                                              const TilePlan&, bool, unsigned*);
 TT_GEMM_INST(double, double, double)
 TT_GEMM_INST(double, double, float)
 TT_GEMM_INST(double, float, double)
@@ -302,14 +323,6 @@ int gemm_fast<double>(cudaStream_t s, int M, int N, int K, double alpha, const d
 }
 
 template <>
-int gemm_fast<float>(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,
-                     int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
-                     int64_t scm, int64_t scn, unsigned* status) {
-  (void)status;
-  return gemm_launch<float, float, float, true>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
-}
-
-template <>
 int gemm_core<double>(cudaStream_t s, int M, int N, int K, double alpha, const double* A, int64_t sam,
                       int64_t sak, const double* B, int64_t sbk, int64_t sbn, double beta, double* C,
                       int64_t scm, int64_t scn, unsigned* status) {
@@ -321,8 +334,16 @@ template <>
 int gemm_core<float>(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,
                      int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
                      int64_t scm, int64_t scn, unsigned* status) {
-  (void)status;
+  if (K >= 16 && sliced_tiles(M, N) >= num_sms())
+    return gemm_sliced(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, status);
   return gemm<float, float, float>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn);
+}
+
+template <>
+int gemm_fast<float>(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam,
+                     int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
+                     int64_t scm, int64_t scn, unsigned* status) {
+  return gemm_core<float>(s, M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, status);
 }
 
 }  // namespace tt

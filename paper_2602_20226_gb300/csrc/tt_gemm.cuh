@@ -33,8 +33,10 @@ int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, i
                  int64_t tiles64, bool compensated = true);
 
 // Dense batched form: prefix (njobs + 1 host ints) = running tile counts for the tile size
-// the plan picks (64 x 64 when they give at least one CTA per SM, else 32 x 32); the same
-// array in device memory goes to gemm_batched_dense, which launches one CTA per real tile.
+// the plan picks (all-FP32 jobs: the sliced tensor-core form, plan.tile == kSlicedPlan,
+// when its tiles give every SM a CTA; otherwise 64 x 64 SIMT tiles when they do, else
+// 32 x 32); the same array in device memory goes to gemm_batched_dense, which launches
+// one CTA per real tile.
 struct TilePlan {
   int tile = 64;
   int64_t total = 0;
@@ -43,7 +45,22 @@ template <typename TA, typename TB, typename TC>
 TilePlan tile_prefix(const GemmJob<TA, TB, TC>* jobs, int njobs, int* prefix);
 template <typename TA, typename TB, typename TC>
 int gemm_batched_dense(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, const int* d_prefix,
-                       const TilePlan& plan, bool compensated = true);
+                       const TilePlan& plan, bool compensated = true, unsigned* status = nullptr);
+
+// FP32 GEMM on the tensor cores in the sliced form (tt_gemm_tc.cu): per 16-wide K block
+// each row of A and column of B is scaled by its own power of two and cut into three
+// 9-bit integer slices; the tensor cores sum the slice products exactly (integers below
+// 2^24) and the block sums are added in float-float.  Error <= ~2^-26 sum_k max|a| max|b|
+// per element, unbiased.  status: ST_TIMEOUT if an mbarrier wait expired (may be null).
+int gemm_sliced(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam, int64_t sak,
+                const float* B, int64_t sbk, int64_t sbn, double beta, float* C, int64_t scm, int64_t scn,
+                unsigned* status);
+// tiles of one job in the sliced form (128 x 64, the short side first when M is short)
+int64_t sliced_tiles(int M, int N);
+// dense batched sliced form: prefix from tile_prefix with plan.tile == kSlicedPlan
+int gemm_sliced_dense(cudaStream_t s, int njobs, const GemmJob<float, float, float>* d_jobs, const int* d_prefix,
+                      int64_t total_tiles, unsigned* status);
+constexpr int kSlicedPlan = 128;
 
 // FP32 GEMM on the tensor cores, TF32 with a 3-term hi/lo split (tt_gemm_tc.cu).
 // acc64: sum the per-K-block tensor-core partials in FP64 registers.
@@ -51,18 +68,21 @@ int gemm_tf32x3(cudaStream_t s, int M, int N, int K, double alpha, const float* 
                 int64_t sak, const float* B, int64_t sbk, int64_t sbn, double beta, float* C,
                 int64_t scm, int64_t scn, unsigned* status, bool acc64 = false);
 
-// The GEMMs that form new cores in the sweeps: FP64 -> SIMT DFMA; FP32 -> SIMT with
-// compensated (Dot2) accumulation.  The 3xTF32 tensor-core path rounds every MMA
-// result toward zero, a bias that grows with K and shrinks the norm of the train by
-// about 1e-7 per sweep step, more than the mixed form's 1e-6 budget allows.
+// The GEMMs that form new cores in the sweeps: FP64 -> SIMT DFMA; FP32 -> the sliced
+// tensor-core form when K >= 16 and its 128 x 64 tiles give every SM a CTA, else SIMT
+// with compensated (Dot2) accumulation (the SIMT tiles spread small products over more
+// SMs: the sliced form took the single-train QR and GEMM phases from 111 to 147 ms).  The 3xTF32
+// tensor-core form is not used: it rounds every MMA result toward zero, a bias that grows
+// with K and shrinks the norm of the train by about 1e-7 per sweep step, more than the
+// mixed form's 1e-6 budget allows; the sliced form's tensor-core sums are exact.
 template <typename T>
 int gemm_core(cudaStream_t s, int M, int N, int K, double alpha, const T* A, int64_t sam, int64_t sak,
               const T* B, int64_t sbk, int64_t sbn, double beta, T* C, int64_t scm, int64_t scn,
               unsigned* status);
 
-// The GEMM inside the Householder QR of each form: FP64 -> SIMT DFMA; FP32 -> SIMT with
-// compensated (Dot2) accumulation: with plain FP32 accumulation of the trailing updates
-// the error of 20..60-site trains at eps = 1e-6 rose from ~2e-6 to 4.6e-6.
+// The GEMM inside the Householder QR of each form: FP64 -> SIMT DFMA; FP32 -> as
+// gemm_core (plain FP32 accumulation of the trailing updates took the error of 20..60-site
+// trains at eps = 1e-6 from ~2e-6 to 4.6e-6: the updates need better than FP32 sums).
 template <typename T>
 int gemm_fast(cudaStream_t s, int M, int N, int K, double alpha, const T* A, int64_t sam, int64_t sak,
               const T* B, int64_t sbk, int64_t sbn, double beta, T* C, int64_t scm, int64_t scn,

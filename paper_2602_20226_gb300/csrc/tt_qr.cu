@@ -463,7 +463,7 @@ int householder_qr(cudaStream_t s, T* A, int m, int n, int lda, QrWork<T>& w) {
     reflector_w_kernel<T, 256><<<nt, 256, 0, s>>>(V, w.ldv, At, lda, mr, jb, Tm, nb, true, w.w2);
     TT_LAUNCH_CHECK();
     // At -= V W2
-    TT_TRY(gemm_fast<T>(s, mr, nt, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, At, 1, lda, nullptr));
+    TT_TRY(gemm_fast<T>(s, mr, nt, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, At, 1, lda, w.status));
   }
   w.m = m;
   w.n = n;
@@ -490,7 +490,7 @@ int form_thin_q(cudaStream_t s, const QrWork<T>& w, T* Q, int ldq) {
     // W2 = T (V^T Qs) ; Qs -= V W2
     reflector_w_kernel<T, 256><<<nc, 256, 0, s>>>(V, w.ldv, Qs, ldq, mr, jb, Tm, nb, false, w.w2);
     TT_LAUNCH_CHECK();
-    TT_TRY(gemm_fast<T>(s, mr, nc, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, Qs, 1, ldq, nullptr));
+    TT_TRY(gemm_fast<T>(s, mr, nc, jb, -1.0, V, 1, w.ldv, w.w2, 1, jb, 1.0, Qs, 1, ldq, w.status));
   }
   return TT_OK;
 }
@@ -553,8 +553,9 @@ void panel_gemm_jobs(const QrJob<T>& J, int j0, int nb, bool formq, PanelGemms<T
   G.m3 = std::max(G.m3, mr);
 }
 
-// FP32: the three GEMMs, compensated (Dot2) - plain FP32 accumulation of the updates took
-// the error of 20..60-site trains at eps = 1e-6 from ~2e-6 to 4.6e-6.  FP64: W2 by the
+// FP32: the three GEMMs in the sliced tensor-core form (exact tensor-core sums; plain FP32
+// accumulation of the updates took the error of 20..60-site trains at eps = 1e-6 from
+// ~2e-6 to 4.6e-6).  FP64: W2 by the
 // reflector kernel (one CTA per column), then the update GEMM - measured faster in FP64,
 // where the work is bound by the FP64 pipe rather than by L2 traffic.
 // d1..d3: the GEMM jobs of every panel ([panel][job]); e1..e3: their tile prefixes
@@ -562,19 +563,20 @@ void panel_gemm_jobs(const QrJob<T>& J, int j0, int nb, bool formq, PanelGemms<T
 template <typename T>
 int apply_panels(cudaStream_t s, const QrJob<T>* d_jobs, int nj, int nb, bool formq, int pn,
                  const GemmJob<T, T, T>* d1, const GemmJob<T, T, T>* d2, const GemmJob<T, T, T>* d3,
-                 const int* e1, const int* e2, const int* e3, const std::vector<PanelGemms<T>>& meta) {
+                 const int* e1, const int* e2, const int* e3, const std::vector<PanelGemms<T>>& meta,
+                 unsigned* status) {
   const PanelGemms<T>& M = meta[pn];
   if (M.n1 <= 0) return TT_OK;
   const size_t jo = (size_t)pn * nj, po = (size_t)pn * (nj + 1);
   if (sizeof(T) == 4) {
-    TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d1 + jo, e1 + po, M.p1)));
-    TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d2 + jo, e2 + po, M.p2)));
+    TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d1 + jo, e1 + po, M.p1, true, status)));
+    TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d2 + jo, e2 + po, M.p2, true, status)));
   } else {
     reflector_w_batched_kernel<T, 256><<<dim3((unsigned)M.n1, (unsigned)nj), 256, 0, s>>>(d_jobs, pn * nb, nb,
                                                                                           formq);
     TT_LAUNCH_CHECK();
   }
-  TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d3 + jo, e3 + po, M.p3)));
+  TT_TRY((gemm_batched_dense<T, T, T>(s, nj, d3 + jo, e3 + po, M.p3, true, status)));
   return TT_OK;
 }
 
@@ -614,7 +616,7 @@ int build_panel_gemms(cudaStream_t s, const std::vector<QrJob<T>>& hj, int nb, b
 
 template <typename T>
 int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
-                           JobArena& arena) {
+                           JobArena& arena, unsigned* status) {
   const int nj = (int)hj.size();
   if (nj == 0) return TT_OK;
   if (nj > 65535) return fail(TT_ERR_UNSUPPORTED, "householder_qr_batched: too many jobs");
@@ -640,14 +642,14 @@ int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, cons
     const size_t smem = std::min(kPanelSmem, (size_t)(m_max - j0) * nb * sizeof(T));
     qr_panel_batched_kernel<T, 512><<<nj, 512, smem, s>>>(d_jobs, j0, nb, smem);
     TT_LAUNCH_CHECK();
-    TT_TRY(apply_panels(s, d_jobs, nj, nb, false, pn, D.d1, D.d2, D.d3, D.e1, D.e2, D.e3, meta));
+    TT_TRY(apply_panels(s, d_jobs, nj, nb, false, pn, D.d1, D.d2, D.d3, D.e1, D.e2, D.e3, meta, status));
   }
   return TT_OK;
 }
 
 template <typename T>
 int form_thin_q_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
-                        JobArena& arena) {
+                        JobArena& arena, unsigned* status) {
   const int nj = (int)hj.size();
   if (nj == 0) return TT_OK;
   int p_max = 0;
@@ -665,18 +667,18 @@ int form_thin_q_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const Q
   PanelArrays<T> D;
   TT_TRY(build_panel_gemms(s, hj, nb, true, npanels, arena, meta, D));
   for (int pn = npanels - 1; pn >= 0; --pn)
-    TT_TRY(apply_panels(s, d_jobs, nj, nb, true, pn, D.d1, D.d2, D.d3, D.e1, D.e2, D.e3, meta));
+    TT_TRY(apply_panels(s, d_jobs, nj, nb, true, pn, D.d1, D.d2, D.d3, D.e1, D.e2, D.e3, meta, status));
   return TT_OK;
 }
 
 template int householder_qr_batched<double>(cudaStream_t, const std::vector<QrJob<double>>&, const QrJob<double>*,
-                                            int, JobArena&);
+                                            int, JobArena&, unsigned*);
 template int householder_qr_batched<float>(cudaStream_t, const std::vector<QrJob<float>>&, const QrJob<float>*,
-                                           int, JobArena&);
+                                           int, JobArena&, unsigned*);
 template int form_thin_q_batched<double>(cudaStream_t, const std::vector<QrJob<double>>&, const QrJob<double>*,
-                                         int, JobArena&);
+                                         int, JobArena&, unsigned*);
 template int form_thin_q_batched<float>(cudaStream_t, const std::vector<QrJob<float>>&, const QrJob<float>*,
-                                        int, JobArena&);
+                                        int, JobArena&, unsigned*);
 template int householder_qr<double>(cudaStream_t, double*, int, int, int, QrWork<double>&);
 template int householder_qr<float>(cudaStream_t, float*, int, int, int, QrWork<float>&);
 template int form_thin_q<double>(cudaStream_t, const QrWork<double>&, double*, int);

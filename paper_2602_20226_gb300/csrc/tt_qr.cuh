@@ -18,6 +18,7 @@ struct QrWork {
   int ldv = 0;
   T* w1 = nullptr;   // [nb * ncols]
   T* w2 = nullptr;   // [nb * ncols]
+  unsigned* status = nullptr;  // device word: ST_TIMEOUT if a tensor-core GEMM's wait expired
   // filled by householder_qr
   int m = 0, n = 0, npanels = 0;
 };
@@ -47,12 +48,13 @@ struct QrJob {
 };
 
 // hj: the jobs on the host (sizes, for the launch shapes and the update GEMMs);
-// d_jobs: the same array in device memory.
+// d_jobs: the same array in device memory; status (may be null): raises ST_TIMEOUT if a
+// tensor-core GEMM's wait expired.
 template <typename T>
 int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
-                           JobArena& arena);
+                           JobArena& arena, unsigned* status = nullptr);
 template <typename T>
 int form_thin_q_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
-                        JobArena& arena);
+                        JobArena& arena, unsigned* status = nullptr);
 
 }  // namespace tt

@@ -74,6 +74,7 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   B.sv.bar = c.take<unsigned>(2);
   B.sv.rot = c.take<unsigned>(SvdWork::kMaxSweeps);
   B.sv.status = c.take<unsigned>(1);
+  B.qr.status = B.sv.status;
   B.sv.sweeps = c.take<int>(1);
   B.sv.norm = c.take<double>(1);
   B.sv.epoch = c.take<unsigned>((size_t)D.r_max + 2);

@@ -1,4 +1,4 @@
-"""GPU checks of the tensor-core (tcgen05, 3xTF32) GEMM and of the mixed form of rounding.
+"""GPU checks of the tensor-core (tcgen05) GEMMs, 3xTF32 and sliced, and of the mixed form of rounding.
 
 GEMM bound: with x = x_hi + x_lo (x_hi = rn_tf32(x), |x_lo| <= 2^-12 |x|), each product
 keeps A_hi B_hi + A_hi B_lo + A_lo B_hi; the dropped A_lo B_lo and the TF32 conversion
@@ -9,14 +9,16 @@ like sqrt(K) 2^-24 times a small factor (measured 4.6e-6 at K = 640); the RMS ch
 allows 4e-7 sqrt(K), far below the ~1e-4 a TF32-only product (lo terms missing) gives.
 
 Mixed rounding: FP32 cores and FP32 QR panels; the QR updates and the core GEMMs use
-compensated FP32 dot products (Dot2), the bond SVD is an FP32 block Jacobi finished by
-FP64 Jacobi sweeps, and sigma, the truncation and the norm are FP64; compared with the
-FP64 oracle run on the same FP32 values.  Stated tolerances: e <= 1e-6 (the target)
+the sliced tensor-core form where its tiles fill the GPU and compensated FP32 dot products
+(Dot2) below that, the bond SVD is an FP32 Jacobi (FP64 Jacobi where it hits its sweep
+cap), and sigma, the truncation and the norm are FP64; compared with the FP64 oracle run
+on the same FP32 values.  Stated tolerances: e <= 1e-6 (the target)
 for the small and ragged trains and for the norm; for the 40-site rank-320 train at
 eps = 1e-6 both results sit up to 1e-6 from the unrounded train, so their distance is
-allowed 4e-6 (measured 2.0e-6 with equal ranks).  The tensor-core GEMM is not on the
+allowed 4e-6 (measured 2.0e-6 with equal ranks).  The 3xTF32 GEMM is not on the
 rounding path: its MMA results are rounded toward zero, a bias that added up to
-1e-5..4e-5 over the 78 sequential QR/GEMM steps of that train.
+1e-5..4e-5 over the 78 sequential QR/GEMM steps of that train.  The sliced form's
+tensor-core sums are sums of small integers, exact whatever the rounding.
 """
 import ctypes
 
@@ -30,7 +32,7 @@ from paper_2602_20226_gb300 import inputs, qtt
 pytestmark = pytest.mark.gpu
 
 
-def _gemm(lib, A, B, C, alpha=1.0, beta=0.0, a_cm=False, b_cm=False):
+def _gemm(lib, A, B, C, alpha=1.0, beta=0.0, a_cm=False, b_cm=False, fn="tt_gemm_f32"):
     M, K = A.shape
     N = B.shape[1]
     Ad = torch.as_tensor(A.T.copy() if a_cm else A, device="cuda")
@@ -38,9 +40,9 @@ def _gemm(lib, A, B, C, alpha=1.0, beta=0.0, a_cm=False, b_cm=False):
     Cd = torch.as_tensor(C, device="cuda")
     sam, sak = (1, M) if a_cm else (K, 1)
     sbk, sbn = (1, K) if b_cm else (N, 1)
-    code = lib.tt_gemm_f32(M, N, K, alpha, ctypes.c_void_p(Ad.data_ptr()), sam, sak,
-                           ctypes.c_void_p(Bd.data_ptr()), sbk, sbn, beta,
-                           ctypes.c_void_p(Cd.data_ptr()), N, 1, None)
+    code = getattr(lib, fn)(M, N, K, alpha, ctypes.c_void_p(Ad.data_ptr() if K else 0), sam, sak,
+                            ctypes.c_void_p(Bd.data_ptr() if K else 0), sbk, sbn, beta,
+                            ctypes.c_void_p(Cd.data_ptr()), N, 1, None)
     assert code == 0, lib.tt_last_error()
     torch.cuda.synchronize()
     return Cd.cpu().numpy()
@@ -163,3 +165,101 @@ def test_mixed_round_noise_level_columns(cuda_lib):
     ref = core.round_tt(y, 1e-6)
     assert all(np.isfinite(c).all() for c in got)
     assert core.rel_err(got, ref) <= 4e-6
+
+
+# ---------------------------------------------------------------- sliced (exact-sum) form
+# Per 16-wide K block: v = 2^(E-9) (h1 + 2^-9 h2 + 2^-18 h3) + d with |d| <= 2^(E-28) and
+# 2^(E-1) <= max|v| < 2^E; the dropped h2 h3, h3 h2, h3 h3 products and the remainders d
+# cost at most 2^-25 max|a| max|b| per product, i.e. 2^-21 per block of 16, plus the final
+# rounding of the result to FP32 (2^-24 |result|).
+
+def _sliced_bound(A, B):
+    K = A.shape[1]
+    A64, B64 = np.abs(A.astype(np.float64)), np.abs(B.astype(np.float64))
+    bound = np.zeros((A.shape[0], B.shape[1]))
+    for k0 in range(0, K, 16):
+        bound += np.outer(A64[:, k0:k0 + 16].max(axis=1), B64[k0:k0 + 16].max(axis=0))
+    return 2.0 ** -21 * bound + 2.0 ** -40 * (A64 @ B64)
+
+
+@pytest.mark.parametrize("M,N,K,a_cm,b_cm", [
+    (128, 64, 16, False, False),   # one tile, one K block
+    (300, 200, 100, True, False),  # ragged tiles and a ragged last K block
+    (64, 1000, 77, False, True),   # short M: computed as C^T = B^T A^T
+    (1000, 40, 640, True, True),
+    (7, 5, 3, False, False),       # K < 16: one partial block
+    (256, 320, 1280, False, False),
+    (33, 17, 2000, False, True),   # long K, one small tile
+])
+def test_gemm_f32_sliced(cuda_lib, M, N, K, a_cm, b_cm):
+    lib = cuda_lib.load()
+    g = np.random.default_rng(M * 11 + N * 5 + K)
+    # magnitudes spread over e^-4..e^4 so that rows and columns get different block exponents
+    A = (g.standard_normal((M, K)) * np.exp(g.uniform(-4, 4, (M, K)))).astype(np.float32)
+    B = (g.standard_normal((K, N)) * np.exp(g.uniform(-4, 4, (1, N)))).astype(np.float32)
+    C0 = g.standard_normal((M, N)).astype(np.float32)
+    got = _gemm(lib, A, B, C0.copy(), 1.5, -0.5, a_cm, b_cm, fn="tt_gemm_f32_sliced")
+    ref = 1.5 * (A.astype(np.float64) @ B.astype(np.float64)) - 0.5 * C0.astype(np.float64)
+    bound = 1.5 * _sliced_bound(A, B) + 2.0 ** -24 * np.abs(ref) + 1e-30
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+    # far inside the bound in the mean: the rounding of the FP32 result dominates
+    assert np.sqrt(np.mean(err ** 2) / np.mean(ref ** 2)) < 2.0 ** -23
+
+
+def test_gemm_f32_sliced_integers_exact(cuda_lib):
+    """Integer operands with every partial sum below 2^24: the exact product, bit for bit."""
+    lib = cuda_lib.load()
+    g = np.random.default_rng(17)
+    A = g.integers(-64, 65, (200, 1000)).astype(np.float32)
+    B = g.integers(-64, 65, (1000, 150)).astype(np.float32)
+    got = _gemm(lib, A, B, np.zeros((200, 150), np.float32), fn="tt_gemm_f32_sliced")
+    ref = A.astype(np.int64) @ B.astype(np.int64)
+    assert np.abs(ref).max() < 2 ** 24
+    assert np.array_equal(got.astype(np.int64), ref)
+
+
+def test_gemm_f32_sliced_unbiased_on_positive_data(cuda_lib):
+    """Sums of positive products, where a rounding bias would add up over K = 4096."""
+    lib = cuda_lib.load()
+    g = np.random.default_rng(23)
+    A = g.uniform(0, 1, (256, 4096)).astype(np.float32)
+    B = g.uniform(0, 1, (4096, 256)).astype(np.float32)
+    got = _gemm(lib, A, B, np.zeros((256, 256), np.float32), fn="tt_gemm_f32_sliced")
+    ref = A.astype(np.float64) @ B.astype(np.float64)
+    rel = (got - ref) / ref
+    assert np.abs(rel).max() <= 2.0 ** -24 + 2.0 ** -30  # the final rounding to FP32
+    assert abs(float(rel.mean())) < 2.0 ** -30
+
+
+def test_gemm_f32_sliced_zero_tiny_rows_and_k0(cuda_lib):
+    lib = cuda_lib.load()
+    g = np.random.default_rng(29)
+    A = g.standard_normal((150, 48)).astype(np.float32)
+    B = g.standard_normal((48, 70)).astype(np.float32)
+    A[3] = 0.0
+    A[5] *= np.float32(2.0 ** -100)   # tiny but above the 2^-118 cut: kept
+    A[7, :16] = 1e-37                 # below the cut in the first K block: counts as zero there
+    got = _gemm(lib, A, B, np.zeros((150, 70), np.float32), fn="tt_gemm_f32_sliced")
+    ref = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.all(got[3] == 0.0)
+    assert np.allclose(got[5], ref[5], rtol=0, atol=2.0 ** -100 * 1e-5)
+    ok = np.ones(150, bool)
+    ok[[3, 5, 7]] = False
+    assert np.all(np.abs(got[ok] - ref[ok]) <= _sliced_bound(A, B)[ok] + 2.0 ** -24 * np.abs(ref[ok]))
+    assert np.abs(got[7] - ref[7]).max() <= 1e-35 + np.abs(ref[7]).max() * 1e-6
+    # K = 0: C <- beta C
+    C0 = g.standard_normal((40, 30)).astype(np.float32)
+    got0 = _gemm(lib, np.zeros((40, 0), np.float32), np.zeros((0, 30), np.float32), C0.copy(), 1.0, 2.0,
+                 fn="tt_gemm_f32_sliced")
+    assert np.array_equal(got0, 2.0 * C0)
+
+
+def test_gemm_f32_sliced_twice_identical(cuda_lib):
+    lib = cuda_lib.load()
+    g = np.random.default_rng(31)
+    A = g.standard_normal((500, 300)).astype(np.float32)
+    B = g.standard_normal((300, 260)).astype(np.float32)
+    a = _gemm(lib, A, B, np.zeros((500, 260), np.float32), fn="tt_gemm_f32_sliced")
+    b = _gemm(lib, A, B, np.zeros((500, 260), np.float32), fn="tt_gemm_f32_sliced")
+    assert np.array_equal(a, b)
