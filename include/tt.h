@@ -248,13 +248,14 @@ int tt_gemm_f32(int32_t M, int32_t N, int32_t K, double alpha, const float* A, i
                 int64_t scm, int64_t scn, void* stream);
 
 /* C = alpha A B + beta C in FP32 on the tensor cores in the sliced form, the GEMM of the
- * mixed form of tt_round and tt_apply_round_batched (K >= 16).  Per 16-wide block of K,
+ * mixed form of tt_apply_round_batched (and of tt_round where its tiles fill the GPU).
+ * Per 32-wide block of K,
  * each row of A and each column of B is scaled by its own power of two and cut into
  * three signed integer slices rounded to nearest (h1 + 2^-9 h2 + 2^-18 h3, |h1| <= 512,
  * |h2|, |h3| <= 256); six TF32 tcgen05 MMAs per K step form three level sums of slice
- * products, integers below 2^23 and therefore exact whatever the tensor core's rounding;
- * the levels are scaled and added in float-float.  Error per element <= 2^-21 sum over
- * 16-wide K blocks of max|a| max|b| (the dropped h2 h3, h3 h2, h3 h3 terms and the last
+ * products, integers below 2^24 and therefore exact whatever the tensor core's rounding;
+ * the levels are scaled and added in float-float.  Error per element <= 2^-20 sum over
+ * 32-wide K blocks of max|a| max|b| (the dropped h2 h3, h3 h2, h3 h3 terms and the last
  * slice's rounding; zero-mean), plus the final rounding to FP32.  Rows or
  * columns whose block maximum is below 2^-118 count as zero in that block.  No
  * counterpart in the paper (Ozaki-type splitting).  Arguments as tt_gemm_f32; K = 0

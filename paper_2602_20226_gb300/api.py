@@ -216,6 +216,26 @@ def tt_eval(x: TT, digits: torch.Tensor, stream=None, out: torch.Tensor | None =
     return out
 
 
+def gemm_f32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, alpha: float = 1.0,
+             beta: float = 0.0, form: str = "sliced", stream=None) -> torch.Tensor:
+    """C = alpha A B + beta C for 2-D FP32 CUDA tensors (any strides) on the tensor cores:
+    form "sliced" (tt_gemm_f32_sliced, exact tensor-core sums) or "tf32x3" (tt_gemm_f32)."""
+    lib = load()
+    fn = {"sliced": "tt_gemm_f32_sliced", "tf32x3": "tt_gemm_f32"}[form]
+    M, K = A.shape
+    N = B.shape[1]
+    if B.shape[0] != K or any(t.dtype != torch.float32 or not t.is_cuda for t in (A, B)):
+        raise ValueError("gemm_f32: A (M, K) and B (K, N) must be FP32 CUDA tensors")
+    if C is None:
+        if beta != 0.0:
+            raise ValueError("gemm_f32: beta != 0 needs C")
+        C = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    _check(fn, getattr(lib, fn)(M, N, K, alpha, ctypes.c_void_p(A.data_ptr()), A.stride(0), A.stride(1),
+                                ctypes.c_void_p(B.data_ptr()), B.stride(0), B.stride(1), beta,
+                                ctypes.c_void_p(C.data_ptr()), C.stride(0), C.stride(1), _stream_ptr(stream)))
+    return C
+
+
 # ---------------------------------------------------------------------------- adjoints
 
 

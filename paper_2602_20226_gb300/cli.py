@@ -12,6 +12,11 @@ each repetition and the output ranks.  `--op hadamard` rounds x (.) x instead.
 
 runs tt_apply_round_batched on the uneven batch instead: trains with L ~ U[20, 60],
 ranks ~ U[8, 128], each with its own random MPO of rank 3..5 (seed 4).
+
+    python -m paper_2602_20226_gb300.cli --gemm 4096 --gemm-form sliced --repeat 10
+
+times one FP32 tensor-core GEMM (N x N x N, N(0, 1) operands, seed 1) with CUDA events
+and prints its TFLOP/s and its largest error against an FP64 product.
 """
 from __future__ import annotations
 
@@ -34,9 +39,13 @@ def main(argv=None) -> None:
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--batch", type=int, default=0, help="trains of the uneven batch (0: one train)")
+    ap.add_argument("--gemm", type=int, default=0, help="size N of one N x N x N FP32 GEMM to time (0: none)")
+    ap.add_argument("--gemm-form", choices=["sliced", "tf32x3"], default="sliced")
     a = ap.parse_args(argv)
     if a.batch > 0:
         return _batch(a)
+    if a.gemm > 0:
+        return _gemm(a)
 
     dtype = torch.float64 if a.form == "fp64" else torch.float32
     prec = _abi.TT_PREC_FP64 if a.form == "fp64" else _abi.TT_PREC_MIXED
@@ -74,6 +83,27 @@ def _batch(a) -> None:
         torch.cuda.synchronize()
         print(f"[{i}] {a.form} batch of {a.batch}: {(time.perf_counter() - t) * 1e3:.1f} ms, "
               f"max rank {max(max(o.ranks) for o in outs)}", flush=True)
+
+
+def _gemm(a) -> None:
+    n = a.gemm
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(n, n, device="cuda", generator=g)
+    B = torch.randn(n, n, device="cuda", generator=g)
+    C = torch.empty(n, n, device="cuda")
+    api.gemm_f32(A, B, C, form=a.gemm_form)  # first launch: configuration, not timed
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.repeat):
+        api.gemm_f32(A, B, C, form=a.gemm_form)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.repeat
+    ref = A.double() @ B.double()
+    err = ((C.double() - ref).abs().max() / ref.abs().max()).item()
+    print(f"{a.gemm_form} gemm n={n}: {ms:.3f} ms, {2.0 * n ** 3 / ms / 1e9:.1f} TFLOP/s, "
+          f"max |C - AB| / max |AB| = {err:.2e}", flush=True)
 
 
 if __name__ == "__main__":

@@ -247,8 +247,10 @@ TilePlan tile_prefix(const GemmJob<TA, TB, TC>* jobs, int njobs, int* prefix) {
     // the sliced tensor-core form when its 128 x 64 tiles give every SM a CTA; below that
     // the SIMT tiles, up to 8x more CTAs, finish first
     int64_t sl = 0;
-    for (int i = 0; i < njobs; ++i)
+    for (int i = 0; i < njobs; ++i) {
       if (jobs[i].K > 0) sl += sliced_tiles(jobs[i].M, jobs[i].N);
+      plan.K_max = std::max(plan.K_max, jobs[i].K);
+    }
     if (sl >= num_sms()) {
       plan.tile = kSlicedPlan;
       int64_t acc = 0;
@@ -281,7 +283,7 @@ int gemm_batched_dense(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_j
                        const TilePlan& plan, bool compensated, unsigned* status) {
   if (njobs <= 0 || plan.total <= 0) return TT_OK;
   if constexpr (std::is_same_v<TA, float> && std::is_same_v<TB, float> && std::is_same_v<TC, float>) {
-    if (plan.tile == kSlicedPlan) return gemm_sliced_dense(s, njobs, d_jobs, d_prefix, plan.total, status);
+    if (plan.tile == kSlicedPlan) return gemm_sliced_dense(s, njobs, d_jobs, d_prefix, plan.total, plan.K_max, status);
   }
   if (plan.total > 0x7fffffff) return fail(TT_ERR_UNSUPPORTED, "gemm_batched_dense: too many tiles");
   const unsigned g = (unsigned)plan.total;

@@ -40,6 +40,7 @@ int gemm_batched(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, i
 struct TilePlan {
   int tile = 64;
   int64_t total = 0;
+  int K_max = 0;  // largest K of the jobs
 };
 template <typename TA, typename TB, typename TC>
 TilePlan tile_prefix(const GemmJob<TA, TB, TC>* jobs, int njobs, int* prefix);
@@ -47,19 +48,21 @@ template <typename TA, typename TB, typename TC>
 int gemm_batched_dense(cudaStream_t s, int njobs, const GemmJob<TA, TB, TC>* d_jobs, const int* d_prefix,
                        const TilePlan& plan, bool compensated = true, unsigned* status = nullptr);
 
-// FP32 GEMM on the tensor cores in the sliced form (tt_gemm_tc.cu): per 16-wide K block
+// FP32 GEMM on the tensor cores in the sliced form (tt_gemm_tc.cu): per 32-wide K block
 // each row of A and column of B is scaled by its own power of two and cut into three
-// 9-bit integer slices; the tensor cores sum the slice products exactly (integers below
-// 2^24) and the block sums are added in float-float.  Error <= ~2^-26 sum_k max|a| max|b|
-// per element, unbiased.  status: ST_TIMEOUT if an mbarrier wait expired (may be null).
+// balanced integer slices; the tensor cores sum the slice products exactly (integers
+// below 2^24) and the block sums are added in float-float.  Error <= ~2^-25 sum_k
+// max|a| max|b| per element (maxima over the K block), zero-mean.  status: ST_TIMEOUT if
+// an mbarrier wait expired (may be null).
 int gemm_sliced(cudaStream_t s, int M, int N, int K, double alpha, const float* A, int64_t sam, int64_t sak,
                 const float* B, int64_t sbk, int64_t sbn, double beta, float* C, int64_t scm, int64_t scn,
                 unsigned* status);
 // tiles of one job in the sliced form (128 x 64, the short side first when M is short)
 int64_t sliced_tiles(int M, int N);
-// dense batched sliced form: prefix from tile_prefix with plan.tile == kSlicedPlan
+// dense batched sliced form: prefix from tile_prefix with plan.tile == kSlicedPlan;
+// K_max >= every job's K (K_max <= 32: the one-block kernel, two CTAs per SM)
 int gemm_sliced_dense(cudaStream_t s, int njobs, const GemmJob<float, float, float>* d_jobs, const int* d_prefix,
-                      int64_t total_tiles, unsigned* status);
+                      int64_t total_tiles, int K_max, unsigned* status);
 constexpr int kSlicedPlan = 128;
 
 // FP32 GEMM on the tensor cores, TF32 with a 3-term hi/lo split (tt_gemm_tc.cu).

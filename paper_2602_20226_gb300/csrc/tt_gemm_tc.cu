@@ -335,7 +335,7 @@ int launch_tc(cudaStream_t s, const TcArgs& a) {
 // Sliced form with exact tensor-core sums (an Ozaki-type splitting: Ozaki, Ogita, Oishi,
 // Rump 2012; Ootomo, Ozaki, Yokota 2024 for integer tensor cores).
 //
-// Per 16-wide K block every row of A and every column of B gets its own power of two
+// Per 32-wide K block every row of A and every column of B gets its own power of two
 // 2^E above its largest magnitude, and each value is cut into three signed integer
 // slices, each rounded to nearest (balanced digits):
 //     v = 2^(E-9) (h1 + 2^-9 h2 + 2^-18 h3) + d,  |h1| <= 512, |h2|, |h3| <= 256,
@@ -343,30 +343,40 @@ int launch_tc(cudaStream_t s, const TcArgs& a) {
 // The slices are small integers, exact in TF32, and the tensor cores form three level
 // sums per block
 //     L0 = sum h1a h1b,  L1 = sum (h1a h2b + h2a h1b),  L2 = sum (h1a h3b + h2a h2b + h3a h1b)
-// whose every partial sum is an integer below 16 * 5 * 2^16 < 2^23: representable in
-// FP32, so the accumulation inside the tensor core is exact whatever its rounding.  The
-// dropped cross terms (h2 h3, h3 h2, h3 h3) and the slice remainders cost at most
-// ~2^-25 of max|a| max|b| per product; balanced digits make them zero-mean, so same-sign
-// data gets no bias.  After each block the threads read the three
-// levels out of tensor memory, scale them by 2^(Ea+Eb-18) (exact) and add them into a
-// float-float (hi, lo) accumulator per output with an error-free TwoSum (Knuth).
-// One CTA of 128 threads owns a 128 x SL_BN tile; the global loads of block k+1 are in
-// flight while block k is sliced and block k-1 drained; the MMAs of block k run while
-// block k+1 is loaded and sliced.  Every mbarrier wait is bounded, as above.
+// whose partial sums are integers of magnitude <= 32 * 2^18 = 2^23 (L0, L1) and
+// <= 32 * 5 * 2^16 < 2^24 (L2): representable in FP32, so the accumulation inside the
+// tensor core is exact whatever its rounding.  The dropped cross terms (h2 h3, h3 h2,
+// h3 h3) and the slice remainders cost at most ~2^-25 of max|a| max|b| per product;
+// balanced digits make them zero-mean, so same-sign data gets no bias.  After each block
+// the threads read the three levels out of tensor memory, scale them by 2^(Ea+Eb-18)
+// (exact) and add them into a float-float (hi, lo) accumulator per output with an
+// error-free TwoSum (Knuth).
+//
+// One CTA of 256 threads (two warpgroups) owns a 128 x SL_BN tile; warpgroup g drains
+// columns [g SL_BN/2, (g+1) SL_BN/2) of the tensor-memory lanes of its warps.  Per block
+// kb: the operand values arrive by cp.async in a padded staging buffer (issued one block
+// ahead), are sliced into the canonical K-major layout of stage kb & 1, and one thread
+// issues the block's 24 MMAs into tensor-memory buffer kb & 1 while the threads drain
+// block kb-1 from the other buffer.  Every mbarrier wait is bounded, as above.
 
-constexpr int SL_BK = 16, SL_BN = 64, SL_RAW = SL_BK + 1;
-constexpr uint32_t SL_TMEM_COLS = 256;  // three level accumulators of SL_BN columns
+constexpr int SL_BK = 32, SL_BN = 64, SL_RAW = SL_BK + 1, SL_THREADS = 256;
 constexpr int SL_A_BYTES = TC_BM * SL_BK * 4, SL_B_BYTES = SL_BN * SL_BK * 4;
 constexpr int SL_STAGE = 3 * SL_A_BYTES + 3 * SL_B_BYTES;
 constexpr int SL_RAW_FLOATS = (TC_BM + SL_BN) * SL_RAW;  // one staging buffer: A rows, then B rows
-constexpr size_t SL_SMEM = 2 * SL_STAGE + 2 * SL_RAW_FLOATS * 4 + 2 * (TC_BM + SL_BN) * 4;
-static_assert(3 * SL_BN <= (int)SL_TMEM_COLS, "tensor memory of the level sums");
-
-// byte offset of element (row, k) of a rows x 16 K-major no-swizzle tile: 8-row x 16-byte
-// core matrices, 128 bytes apart along K and 512 bytes apart along the rows
-__device__ __forceinline__ uint32_t tile16_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+// NST stages (and tensor-memory buffers): 2 for the pipelined K loop, 1 when K fits one
+// block (then two CTAs share an SM: shared memory below half of it, 256 TMEM columns)
+template <int NST>
+__host__ __device__ constexpr size_t sl_smem() {
+  return NST * SL_STAGE + NST * SL_RAW_FLOATS * 4 + NST * (TC_BM + SL_BN) * 4;
 }
+template <int NST>
+__host__ __device__ constexpr uint32_t sl_tmem_cols() {
+  return NST == 2 ? 512u : 256u;
+}
+static_assert(2 * 3 * SL_BN <= (int)sl_tmem_cols<2>() && 3 * SL_BN <= (int)sl_tmem_cols<1>(),
+              "tensor memory of the level sums");
+static_assert(sl_smem<2>() <= 227 * 1024, "shared memory of the sliced GEMM");
+static_assert(2 * (sl_smem<1>() + 2048) <= 228 * 1024, "two one-block CTAs per SM");
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, int bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
@@ -375,35 +385,46 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, int byte
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Asynchronous copy of one rows x 16 block of an operand whose element (row, k) is
-// P[row*srow + k*sk] into raw (row stride SL_RAW), in a coalesced order; zero-filled
-// beyond nrows / K (those copies read nothing and point at P itself).
+// Asynchronous copy of one rows x 32 block of an operand whose element (row, k) is
+// P[row*srow + k*sk] into raw (row stride SL_RAW): a warp copies 32 consecutive k of one
+// row, or 32 consecutive rows of one k when the rows are contiguous.  Zero-filled beyond
+// nrows / K (those copies read nothing and point at P itself).
 template <int ROWS>
 __device__ __forceinline__ void raw_prefetch(const float* __restrict__ P, int64_t srow, int64_t sk, int row0,
                                              int nrows, int k0, int K, float* raw) {
-  constexpr int PER = ROWS * SL_BK / TC_THREADS;
+  constexpr int PER = ROWS * SL_BK / SL_THREADS;
   const int tid = threadIdx.x;
   const bool kfast = (sk == 1 || srow != 1);
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    const int e = tid + u * TC_THREADS;
-    const int r = kfast ? (e >> 4) : (e % ROWS), k = kfast ? (e & 15) : (e / ROWS);
+    const int e = tid + u * SL_THREADS;
+    const int r = kfast ? (e >> 5) : (e % ROWS), k = kfast ? (e & 31) : (e / ROWS);
     const int gr = row0 + r, gk = k0 + k;
     const bool in = gr < nrows && gk < K;
     cp_async4(raw + r * SL_RAW + k, in ? P + (int64_t)gr * srow + (int64_t)gk * sk : P, in ? 4 : 0);
   }
 }
 
-// Cut the rows x 16 block in raw (row stride SL_RAW) into three integer slices stored in
-// the canonical layout at s0 / s1 / s2, and the row's output scale 2^(E-9) in pscale.
-// A row whose largest magnitude is below 2^-118 (or zero) gets zero slices and scale 0.
+// byte offset of element (row, k) of a rows x 32 K-major no-swizzle tile (8-row x 16-byte
+// core matrices, 128 bytes apart along K, 1024 bytes apart along the rows)
+__device__ __forceinline__ uint32_t tile32_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// Cut the rows x 32 block in raw into three integer slices stored in the canonical layout
+// at s0 / s1 / s2, and each row's output scale 2^(E-9) in pscale.  TPR threads share a
+// row: lane = part * (32 / TPR) + row-in-warp, so that the staging reads and the 16-byte
+// slice stores of a warp hit distinct banks.  A row whose largest magnitude is below
+// 2^-118 (or zero) gets zero slices and scale 0.
 template <int ROWS>
 __device__ __forceinline__ void slice_rows(const float* raw, uint8_t* s0, uint8_t* s1, uint8_t* s2,
                                            float* pscale) {
-  constexpr int TPR = TC_THREADS / ROWS;  // threads per row: 1 or 2 (adjacent lanes)
-  constexpr int KPT = SL_BK / TPR;
-  static_assert(TPR * ROWS == TC_THREADS && KPT % 4 == 0, "slice layout");
-  const int tid = threadIdx.x, row = tid / TPR, part = tid % TPR;
+  constexpr int TPR = SL_THREADS / ROWS;  // threads per row: 2 (A) or 4 (B)
+  constexpr int KPT = SL_BK / TPR;        // 16 or 8
+  constexpr int RPW = 32 / TPR;           // rows per warp
+  static_assert(TPR * ROWS == SL_THREADS && KPT % 4 == 0, "slice layout");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = warp * RPW + lane % RPW, part = lane / RPW;
   float v[KPT];
   float m = 0.0f;
 #pragma unroll
@@ -411,7 +432,8 @@ __device__ __forceinline__ void slice_rows(const float* raw, uint8_t* s0, uint8_
     v[j] = raw[row * SL_RAW + part * KPT + j];
     m = fmaxf(m, fabsf(v[j]));
   }
-  if (TPR == 2) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+#pragma unroll
+  for (int off = RPW; off < 32; off <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
   // biased exponent eb of the largest magnitude: m < 2^E with E = eb - 126
   const uint32_t eb = __float_as_uint(m) >> 23;
   const bool live = eb >= 9u;
@@ -434,7 +456,7 @@ __device__ __forceinline__ void slice_rows(const float* raw, uint8_t* s0, uint8_
       pb[t] = h2;
       pc[t] = rintf(z);
     }
-    const uint32_t o = tile16_off(row, part * KPT + 4 * q);
+    const uint32_t o = tile32_off(row, part * KPT + 4 * q);
     *reinterpret_cast<float4*>(s0 + o) = a;
     *reinterpret_cast<float4*>(s1 + o) = b;
     *reinterpret_cast<float4*>(s2 + o) = c;
@@ -453,13 +475,16 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Add one block's three levels (tensor-memory columns [l*SL_BN, (l+1)*SL_BN)) into the
-// float-float accumulators of this thread's row; nvalid = columns of the tile inside N.
+constexpr int SL_HALF = SL_BN / 2;  // columns drained by one warpgroup
+
+// Add one block's three levels (tensor-memory columns buf + l*SL_BN + c of this warp's
+// lanes, c in this warpgroup's half) into the float-float accumulators of this thread's
+// row; nvalid = columns of this warpgroup's half inside N.
 __device__ __forceinline__ void drain_levels(uint32_t lane_base, float pa, const float* pb, int nvalid,
-                                             float (&hi)[SL_BN], float (&lo)[SL_BN]) {
+                                             float (&hi)[SL_HALF], float (&lo)[SL_HALF]) {
 #pragma unroll
-  for (int c0 = 0; c0 < SL_BN; c0 += 16) {
-    if (c0 < nvalid) {  // uniform across the CTA
+  for (int c0 = 0; c0 < SL_HALF; c0 += 16) {
+    if (c0 < nvalid) {  // uniform across the warpgroup
       uint32_t r0[16], r1[16];
       tmem_ld16_issue(lane_base + (uint32_t)c0, r0);
       tmem_ld16_issue(lane_base + (uint32_t)(SL_BN + c0), r1);
@@ -468,35 +493,38 @@ __device__ __forceinline__ void drain_levels(uint32_t lane_base, float pa, const
       for (int j = 0; j < 16; ++j) {
         const float sc = __fmul_rn(pa, pb[c0 + j]);  // 2^(Ea+Eb-18), exact
         const float t0 = __fmul_rn(__uint_as_float(r0[j]), sc);
-        const float t1 = __fmul_rn(__uint_as_float(r1[j]), __fmul_rn(sc, 0x1p-9f));
         // TwoSum: hi + t0 = ss + e exactly
         const float h = hi[c0 + j];
         const float ss = __fadd_rn(h, t0);
         const float bb = __fsub_rn(ss, h);
         const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(ss, bb)), __fsub_rn(t0, bb));
         hi[c0 + j] = ss;
-        lo[c0 + j] = __fadd_rn(lo[c0 + j], __fadd_rn(e, t1));
+        lo[c0 + j] = __fmaf_rn(__uint_as_float(r1[j]), __fmul_rn(sc, 0x1p-9f), __fadd_rn(lo[c0 + j], e));
       }
       tmem_ld16_issue(lane_base + (uint32_t)(2 * SL_BN + c0), r0);
       tmem_wait_ld();
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const float sc = __fmul_rn(pa, pb[c0 + j]);
-        lo[c0 + j] = __fadd_rn(lo[c0 + j], __fmul_rn(__uint_as_float(r0[j]), __fmul_rn(sc, 0x1p-18f)));
+        lo[c0 + j] = __fmaf_rn(__uint_as_float(r0[j]), __fmul_rn(sc, 0x1p-18f), lo[c0 + j]);
       }
     }
   }
 }
 
-// One 128 x SL_BN output tile at (m0, n0) of C = alpha A B + beta C.  Called by all 128
-// threads of the CTA; allocates and frees SL_TMEM_COLS columns of tensor memory.
+// One 128 x SL_BN output tile at (m0, n0) of C = alpha A B + beta C.  Called by all
+// SL_THREADS threads of the CTA; allocates and frees sl_tmem_cols<NST>() columns of tensor
+// memory.  NST = 1 requires K <= SL_BK.
+template <int NST>
 __device__ __forceinline__ void sliced_tile(const TcArgs& g, int m0, int n0, uint8_t* smem) {
   constexpr uint32_t IDESC = idesc_tf32(SL_BN);
-  __shared__ uint64_t mbar;
+  constexpr uint32_t SL_TMEM_COLS = sl_tmem_cols<NST>();
+  __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  float* raw = reinterpret_cast<float*>(smem + 2 * SL_STAGE);  // [2][SL_RAW_FLOATS] staging
-  float* scl = raw + 2 * SL_RAW_FLOATS;  // [stage][TC_BM + SL_BN]: row scales of A, then of B
+  float* raw = reinterpret_cast<float*>(smem + NST * SL_STAGE);  // [NST][SL_RAW_FLOATS] staging
+  float* scl = raw + NST * SL_RAW_FLOATS;  // [stage][TC_BM + SL_BN]: row scales of A, then of B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wg = warp >> 2, wq = warp & 3;  // warpgroup, warp within it (its 32 TMEM lanes)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -506,92 +534,103 @@ __device__ __forceinline__ void sliced_tile(const TcArgs& g, int m0, int n0, uin
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&mbar);
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-  const int nvalid = g.N - n0;
+  const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(wg * SL_HALF);
+  const int row_l = wq * 32 + lane;  // this thread's row of the tile
+  const int nvalid = g.N - n0 - wg * SL_HALF;
 
-  float hi[SL_BN], lo[SL_BN];
+  float hi[SL_HALF], lo[SL_HALF];
 #pragma unroll
-  for (int j = 0; j < SL_BN; ++j) hi[j] = lo[j] = 0.0f;
-  const int nkb = (g.K + SL_BK - 1) / SL_BK;
+  for (int j = 0; j < SL_HALF; ++j) hi[j] = lo[j] = 0.0f;
+  const int nkb = NST == 1 ? (g.K > 0 ? 1 : 0) : (g.K + SL_BK - 1) / SL_BK;
   raw_prefetch<TC_BM>(g.A, g.sam, g.sak, m0, g.M, 0, g.K, raw);
   raw_prefetch<SL_BN>(g.B, g.sbn, g.sbk, n0, g.N, 0, g.K, raw + TC_BM * SL_RAW);
   cp_async_commit();
-  uint32_t phase = 0;
+  uint32_t phase0 = 0, phase1 = 0;
   bool ok = true;
   for (int kb = 0; kb < nkb; ++kb) {
-    const int s = kb & 1;
+    const int s = NST == 1 ? 0 : (kb & 1);
     uint8_t* st = smem + s * SL_STAGE;
-    float* sc_s = scl + s * (TC_BM + SL_BN);
     float* rs = raw + s * SL_RAW_FLOATS;
     cp_async_wait_all();
     __syncthreads();  // block kb staged in rs; the other buffer was last read by the slicing of kb-1
-    if (kb + 1 < nkb) {  // next block's copies in flight during the slicing and the drain
+    if (NST == 2 && kb + 1 < nkb) {  // next block's copies in flight during the slicing and the drain
       float* rn = raw + (s ^ 1) * SL_RAW_FLOATS;
       raw_prefetch<TC_BM>(g.A, g.sam, g.sak, m0, g.M, (kb + 1) * SL_BK, g.K, rn);
       raw_prefetch<SL_BN>(g.B, g.sbn, g.sbk, n0, g.N, (kb + 1) * SL_BK, g.K, rn + TC_BM * SL_RAW);
       cp_async_commit();
     }
-    // stage s was last read by the MMAs of block kb-2, finished before block kb-2 was drained
+    // stage s and tensor-memory buffer s were last used by block kb-2: its MMAs finished
+    // and its levels were drained in the previous iteration, before the barrier above
+    float* sc_s = scl + s * (TC_BM + SL_BN);
     slice_rows<TC_BM>(rs, st, st + SL_A_BYTES, st + 2 * SL_A_BYTES, sc_s);
     slice_rows<SL_BN>(rs + TC_BM * SL_RAW, st + 3 * SL_A_BYTES, st + 3 * SL_A_BYTES + SL_B_BYTES,
                       st + 3 * SL_A_BYTES + 2 * SL_B_BYTES, sc_s + TC_BM);
     fence_async_smem();
-    if (kb > 0) {  // drain block kb-1 (its levels must be read before block kb overwrites them)
-      const bool w = mbar_wait(&mbar, phase);
-      ok = __syncthreads_and(w);
-      if (!ok) break;  // phase stays that of the MMAs still in flight
-      phase ^= 1;
-      tc_fence_after();
-      const float* sp = scl + (s ^ 1) * (TC_BM + SL_BN);
-      drain_levels(lane_base, sp[warp * 32 + lane], sp + TC_BM, nvalid, hi, lo);
-      tc_fence_before();
-    }
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(st), b0 = a0 + 3 * SL_A_BYTES;
+      const uint32_t d0 = tmem + (uint32_t)(s * 3 * SL_BN);
 #pragma unroll
       for (int kk = 0; kk < SL_BK / 8; ++kk) {
         const uint32_t off = kk * 256;  // two core matrices along K per MMA
-        const uint64_t da[3] = {smem_desc(a0 + off, 128, 512), smem_desc(a0 + SL_A_BYTES + off, 128, 512),
-                                smem_desc(a0 + 2 * SL_A_BYTES + off, 128, 512)};
-        const uint64_t db[3] = {smem_desc(b0 + off, 128, 512), smem_desc(b0 + SL_B_BYTES + off, 128, 512),
-                                smem_desc(b0 + 2 * SL_B_BYTES + off, 128, 512)};
+        const uint64_t da0 = smem_desc(a0 + off, 128, 1024), da1 = smem_desc(a0 + SL_A_BYTES + off, 128, 1024),
+                       da2 = smem_desc(a0 + 2 * SL_A_BYTES + off, 128, 1024);
+        const uint64_t db0 = smem_desc(b0 + off, 128, 1024), db1 = smem_desc(b0 + SL_B_BYTES + off, 128, 1024),
+                       db2 = smem_desc(b0 + 2 * SL_B_BYTES + off, 128, 1024);
         const uint32_t acc = kk > 0 ? 1u : 0u;
-        mma_tf32(tmem, da[0], db[0], IDESC, acc);                             // L0
-        mma_tf32(tmem + SL_BN, da[0], db[1], IDESC, acc);                     // L1
-        mma_tf32(tmem + SL_BN, da[1], db[0], IDESC, 1u);
-        mma_tf32(tmem + 2 * SL_BN, da[0], db[2], IDESC, acc);                 // L2
-        mma_tf32(tmem + 2 * SL_BN, da[1], db[1], IDESC, 1u);
-        mma_tf32(tmem + 2 * SL_BN, da[2], db[0], IDESC, 1u);
+        mma_tf32(d0, da0, db0, IDESC, acc);                   // L0
+        mma_tf32(d0 + SL_BN, da0, db1, IDESC, acc);           // L1
+        mma_tf32(d0 + SL_BN, da1, db0, IDESC, 1u);
+        mma_tf32(d0 + 2 * SL_BN, da0, db2, IDESC, acc);       // L2
+        mma_tf32(d0 + 2 * SL_BN, da1, db1, IDESC, 1u);
+        mma_tf32(d0 + 2 * SL_BN, da2, db0, IDESC, 1u);
       }
-      mma_commit(&mbar);
+      mma_commit(&mbar[s]);
+    }
+    if (NST == 2 && kb > 0) {  // drain block kb-1 from buffer s^1 while block kb's MMAs run
+      const int sp = s ^ 1;
+      const bool w = sp == 0 ? mbar_wait(&mbar[0], phase0) : mbar_wait(&mbar[1], phase1);
+      ok = __syncthreads_and(w);
+      if (!ok) break;
+      if (sp == 0) phase0 ^= 1; else phase1 ^= 1;
+      tc_fence_after();
+      const float* sp_s = scl + sp * (TC_BM + SL_BN);
+      drain_levels(lane_base + (uint32_t)(sp * 3 * SL_BN), sp_s[row_l], sp_s + TC_BM + wg * SL_HALF, nvalid, hi,
+                   lo);
+      tc_fence_before();
     }
   }
   if (ok && nkb > 0) {
-    const bool w = mbar_wait(&mbar, phase);
+    const int sp = NST == 1 ? 0 : ((nkb - 1) & 1);
+    const bool w = sp == 0 ? mbar_wait(&mbar[0], phase0) : mbar_wait(&mbar[1], phase1);
     ok = __syncthreads_and(w);
     if (ok) {
       tc_fence_after();
-      const float* sp = scl + ((nkb - 1) & 1) * (TC_BM + SL_BN);
-      drain_levels(lane_base, sp[warp * 32 + lane], sp + TC_BM, nvalid, hi, lo);
+      const float* sp_s = scl + sp * (TC_BM + SL_BN);
+      drain_levels(lane_base + (uint32_t)(sp * 3 * SL_BN), sp_s[row_l], sp_s + TC_BM + wg * SL_HALF, nvalid, hi,
+                   lo);
     }
-  } else if (!ok) {
-    mbar_wait(&mbar, phase);  // the MMAs in flight: a bounded chance to finish before the free
+  }
+  if (!ok) {
+    // a wait expired: give the MMAs in flight a bounded chance to finish before the free
+    mbar_wait(&mbar[0], phase0);
+    if (NST == 2) mbar_wait(&mbar[1], phase1);
   }
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
+    const int row = m0 + row_l;
     if (row < g.M) {
 #pragma unroll
-      for (int j = 0; j < SL_BN; ++j) {
-        const int col = n0 + j;
+      for (int j = 0; j < SL_HALF; ++j) {
+        const int col = n0 + wg * SL_HALF + j;
         if (col < g.N) {
           float* p = g.C + (int64_t)row * g.scm + (int64_t)col * g.scn;
           double v = g.alpha * ((double)hi[j] + (double)lo[j]);
@@ -621,14 +660,16 @@ __host__ __device__ __forceinline__ TcArgs sliced_args(int M, int N, int K, doub
   return TcArgs{M, N, K, alpha, beta, A, sam, sak, B, sbk, sbn, C, scm, scn, status};
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 2) gemm_sliced_kernel(TcArgs g) {
+template <int NST>
+__global__ void __launch_bounds__(SL_THREADS, 3 - NST) gemm_sliced_kernel(TcArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  sliced_tile(g, blockIdx.y * TC_BM, blockIdx.x * SL_BN, smem);
+  sliced_tile<NST>(g, blockIdx.y * TC_BM, blockIdx.x * SL_BN, smem);
 }
 
 // one CTA per tile of every job: prefix[j] = first tile of job j (tiles of the swapped
 // problem when sliced_swap holds)
-__global__ void __launch_bounds__(TC_THREADS, 2)
+template <int NST>
+__global__ void __launch_bounds__(SL_THREADS, 3 - NST)
     gemm_sliced_dense_kernel(const GemmJob<float, float, float>* __restrict__ jobs, const int* __restrict__ prefix,
                              int njobs, unsigned* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -640,7 +681,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     else hi = mid;
   }
   // the job's arguments live in shared memory (uniform, read where used) rather than in
-  // ~30 registers next to the 128 accumulator registers of each thread
+  // ~30 registers of every thread
   __shared__ TcArgs sg;
   if (threadIdx.x == 0) {
     const GemmJob<float, float, float> j = jobs[lo];
@@ -649,16 +690,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   __syncthreads();
   const int local = id - prefix[lo];
   const int tn = (sg.N + SL_BN - 1) / SL_BN;
-  sliced_tile(sg, (local / tn) * TC_BM, (local % tn) * SL_BN, smem);
+  sliced_tile<NST>(sg, (local / tn) * TC_BM, (local % tn) * SL_BN, smem);
 }
 
-template <typename K>
+template <int NST, typename K>
 int sliced_configure(K kernel) {
   static int configured = -1;
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {
-    TT_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL_SMEM));
+    TT_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl_smem<NST>()));
     configured = dev;
   }
   return TT_OK;
@@ -702,18 +743,29 @@ int gemm_sliced(cudaStream_t s, int M, int N, int K, double alpha, const float* 
   const TcArgs a = sliced_args(M, N, K, alpha, A, sam, sak, B, sbk, sbn, beta, C, scm, scn, status);
   dim3 grid((unsigned)ceil_div(a.N, SL_BN), (unsigned)ceil_div(a.M, TC_BM));
   if (grid.y > 65535u) return fail(TT_ERR_UNSUPPORTED, "gemm_sliced: M too large");
-  TT_TRY(sliced_configure(gemm_sliced_kernel));
-  gemm_sliced_kernel<<<grid, TC_THREADS, SL_SMEM, s>>>(a);
+  if (K <= SL_BK) {
+    TT_TRY(sliced_configure<1>(gemm_sliced_kernel<1>));
+    gemm_sliced_kernel<1><<<grid, SL_THREADS, sl_smem<1>(), s>>>(a);
+  } else {
+    TT_TRY(sliced_configure<2>(gemm_sliced_kernel<2>));
+    gemm_sliced_kernel<2><<<grid, SL_THREADS, sl_smem<2>(), s>>>(a);
+  }
   TT_LAUNCH_CHECK();
   return TT_OK;
 }
 
 int gemm_sliced_dense(cudaStream_t s, int njobs, const GemmJob<float, float, float>* d_jobs, const int* d_prefix,
-                      int64_t total_tiles, unsigned* status) {
+                      int64_t total_tiles, int K_max, unsigned* status) {
   if (njobs <= 0 || total_tiles <= 0) return TT_OK;
   if (total_tiles > 0x7fffffff) return fail(TT_ERR_UNSUPPORTED, "gemm_sliced_dense: too many tiles");
-  TT_TRY(sliced_configure(gemm_sliced_dense_kernel));
-  gemm_sliced_dense_kernel<<<(unsigned)total_tiles, TC_THREADS, SL_SMEM, s>>>(d_jobs, d_prefix, njobs, status);
+  const unsigned g = (unsigned)total_tiles;
+  if (K_max <= SL_BK) {
+    TT_TRY(sliced_configure<1>(gemm_sliced_dense_kernel<1>));
+    gemm_sliced_dense_kernel<1><<<g, SL_THREADS, sl_smem<1>(), s>>>(d_jobs, d_prefix, njobs, status);
+  } else {
+    TT_TRY(sliced_configure<2>(gemm_sliced_dense_kernel<2>));
+    gemm_sliced_dense_kernel<2><<<g, SL_THREADS, sl_smem<2>(), s>>>(d_jobs, d_prefix, njobs, status);
+  }
   TT_LAUNCH_CHECK();
   return TT_OK;
 }

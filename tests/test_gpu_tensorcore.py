@@ -168,26 +168,27 @@ def test_mixed_round_noise_level_columns(cuda_lib):
 
 
 # ---------------------------------------------------------------- sliced (exact-sum) form
-# Per 16-wide K block: v = 2^(E-9) (h1 + 2^-9 h2 + 2^-18 h3) + d with |d| <= 2^(E-28) and
+# Per 32-wide K block: v = 2^(E-9) (h1 + 2^-9 h2 + 2^-18 h3) + d with |d| <= 2^(E-28) and
 # 2^(E-1) <= max|v| < 2^E; the dropped h2 h3, h3 h2, h3 h3 products and the remainders d
-# cost at most 2^-25 max|a| max|b| per product, i.e. 2^-21 per block of 16, plus the final
+# cost at most 2^-25 max|a| max|b| per product, i.e. 2^-20 per block of 32, plus the final
 # rounding of the result to FP32 (2^-24 |result|).
 
 def _sliced_bound(A, B):
     K = A.shape[1]
     A64, B64 = np.abs(A.astype(np.float64)), np.abs(B.astype(np.float64))
     bound = np.zeros((A.shape[0], B.shape[1]))
-    for k0 in range(0, K, 16):
-        bound += np.outer(A64[:, k0:k0 + 16].max(axis=1), B64[k0:k0 + 16].max(axis=0))
-    return 2.0 ** -21 * bound + 2.0 ** -40 * (A64 @ B64)
+    for k0 in range(0, K, 32):
+        bound += np.outer(A64[:, k0:k0 + 32].max(axis=1), B64[k0:k0 + 32].max(axis=0))
+    return 2.0 ** -20 * bound + 2.0 ** -40 * (A64 @ B64)
 
 
 @pytest.mark.parametrize("M,N,K,a_cm,b_cm", [
-    (128, 64, 16, False, False),   # one tile, one K block
+    (128, 64, 32, False, False),   # one tile, one K block
+    (256, 128, 16, True, True),    # one partial K block
     (300, 200, 100, True, False),  # ragged tiles and a ragged last K block
     (64, 1000, 77, False, True),   # short M: computed as C^T = B^T A^T
     (1000, 40, 640, True, True),
-    (7, 5, 3, False, False),       # K < 16: one partial block
+    (7, 5, 3, False, False),       # K < 32: one partial block
     (256, 320, 1280, False, False),
     (33, 17, 2000, False, True),   # long K, one small tile
 ])
@@ -239,7 +240,7 @@ def test_gemm_f32_sliced_zero_tiny_rows_and_k0(cuda_lib):
     B = g.standard_normal((48, 70)).astype(np.float32)
     A[3] = 0.0
     A[5] *= np.float32(2.0 ** -100)   # tiny but above the 2^-118 cut: kept
-    A[7, :16] = 1e-37                 # below the cut in the first K block: counts as zero there
+    A[7, :32] = 1e-37                 # below the cut in the first K block: counts as zero there
     got = _gemm(lib, A, B, np.zeros((150, 70), np.float32), fn="tt_gemm_f32_sliced")
     ref = A.astype(np.float64) @ B.astype(np.float64)
     assert np.all(got[3] == 0.0)
