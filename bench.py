@@ -5,8 +5,10 @@ One step = y = W x (MPO apply) followed by y' = round(y, eps) on one TT, all thr
 the libtt C ABI.  Default workload: 2D quantics TT, 2 x 20 bits interleaved (L = 40),
 d = 2, rank 64 (seeded Gaussian cores), the 2D Dirichlet Laplacian MPO (rank 5,
 pre-round rank 320), eps = 1e-8, the plain FP64 form.  Alongside, the same step in the
-mixed form (FP32 cores, compensated-FP32 GEMMs, FP64-finished bond SVDs), its speed-up over FP64 and
-its error against the FP64 oracle.
+mixed form (FP32 cores; FP32 GEMMs with better-than-FP32 sums: the sliced tensor-core
+form or compensated SIMT; FP32 bond SVDs with FP64 singular values and truncation), its
+speed-up over FP64 and its error against the FP64 oracle, and the batched apply + round
+of the uneven 512-train batch in both forms.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica (a single TT's sweeps are a
@@ -304,7 +306,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def bench_batched(tt, dev, warm, n_tt=128, nstreams=5, n_err=4, rank=0, world=1):
+def bench_batched(tt, dev, warm, n_tt=512, nstreams=5, n_err=4, rank=0, world=1):
     """Uneven batch (L ~ U[20,60], rank ~ U[8,128], MPO rank ~ U{3,4,5}), eps = 1e-6, through
     tt_apply_round_batched (lock-step over the trains): the mixed form (FP32 cores) against
     the FP64 form on the same trains, and the mixed results' error against the oracle on
@@ -460,8 +462,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--batch-trains", type=int, default=128,
-                    help="trains in the secondary batched workload (the full batch is 512)")
+    ap.add_argument("--batch-trains", type=int, default=512,
+                    help="trains in the secondary batched workload (default: the full batch of 512)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

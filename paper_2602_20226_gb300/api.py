@@ -313,13 +313,26 @@ def tt_apply_round_batched(Ws: list, xs: list, eps: float, max_rank: int = 0, pr
         prec = _abi.TT_PREC_FP64 if dtype == torch.float64 else _abi.TT_PREC_MIXED
     wd = [_desc(W) for W in Ws]
     xd = [_desc(x) for x in xs]
+    # the apply outputs and the rounded results of all trains are carved from two flat
+    # buffers (two allocations per call instead of two per core); each core starts on a
+    # 256-byte boundary
+    rks = [[a * b for a, b in zip(W.ranks, x.ranks)] for W, x in zip(Ws, xs)]
+    quantum = 256 // torch.empty((), dtype=dtype).element_size()
+    sizes = [[-(-(r[k] * x.dims[k] * r[k + 1]) // quantum) * quantum for k in range(x.L)] for r, x in zip(rks, xs)]
+    total = sum(sum(z) for z in sizes)
+    yflat = torch.empty(max(total, 1), dtype=dtype, device=dev)
+    oflat = torch.empty(max(total, 1), dtype=dtype, device=dev)
     ys, yd, ob, od = [], [], [], []
-    for W, x in zip(Ws, xs):
-        r = [a * b for a, b in zip(W.ranks, x.ranks)]
-        y = [torch.empty((r[k], x.dims[k], r[k + 1]), dtype=dtype, device=dev) for k in range(x.L)]
+    off = 0
+    for x, r, z in zip(xs, rks, sizes):
+        y, bufs = [], []
+        for k in range(x.L):
+            m = r[k] * x.dims[k] * r[k + 1]
+            y.append(yflat[off: off + m].view(r[k], x.dims[k], r[k + 1]))
+            bufs.append(oflat[off: off + m])
+            off += z[k]
         ys.append(y)
         yd.append(_Desc(y, x.dims, r, dtype))
-        bufs = [torch.empty(c.numel(), dtype=dtype, device=dev) for c in y]
         ob.append(bufs)
         od.append(_Desc(bufs, x.dims, r, dtype))
     Warr = (_abi.tt_mpo * n)(*[d.s for d in wd])
