@@ -319,7 +319,9 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
   tm.mark(1);
 
   // ---- 3. left-to-right truncated SVD sweep
-  const double unit = kMixed ? 1.1920928955078125e-07 : 2.220446049250313e-16;
+  // certificate: FP64 arithmetic in both forms (the mixed form certifies its stored FP32
+  // factor, whose singular values its truncation uses, against delta and the 2^-22 floor)
+  const double unit = 2.220446049250313e-16;
   for (int k = 0; k + 1 < Lmax; ++k) {
     std::vector<int> act;
     for (int i = 0; i < n; ++i)
@@ -377,14 +379,15 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     TT_TRY((map_batched<T, double>(s, na, d_xext, mx_x)));
     tm.mark(2);
 
-    // delta_scale = eps / sqrt(L_i - 1) differs between trains of different length; the
-    // kernels that use it are launched once per length present in the step
+    // delta_scale = eps / sqrt(L_i - 1) differs between trains of different length: each
+    // job carries its own, so one launch serves all trains of a size class
     std::vector<SvdJob> sj(na);
     for (int a = 0; a < na; ++a) {
       TrainState<T>& S = tr[act[a]];
       Bufs<T>& B = S.B;
       sj[a] = SvdJob{B.sv.X, pp_[a], pp_[a], B.X32, pp_[a], B.sv.sigma, B.sv.perm, B.sv.rank,
-                     B.sv.status, B.sv.sweeps, B.sv.norm, 0, B.vsel};
+                     B.sv.status, B.sv.sweeps, B.sv.norm, 0, B.vsel,
+                     eps / std::sqrt((double)std::max(S.L - 1, 1))};
     }
     // ---- certificate (tall bonds, max_rank not binding, when it can succeed at all:
     // it subtracts p u ||R||_F, so it needs p u < delta / ||x||)
@@ -401,26 +404,11 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
         }
       }
       if (!cj.empty()) {
-        // one launch per train length (its delta_scale)
-        std::vector<int> order(cj.size());
-        for (size_t q = 0; q < cj.size(); ++q) order[q] = (int)q;
-        std::sort(order.begin(), order.end(), [&](int u, int v) { return tr[act[cidx[u]]].L < tr[act[cidx[v]]].L; });
-        size_t g0 = 0;
-        while (g0 < order.size()) {
-          const int Lg = tr[act[cidx[order[g0]]]].L;
-          size_t g1 = g0;
-          std::vector<SvdJob> grp;
-          int gmax = 0;
-          while (g1 < order.size() && tr[act[cidx[order[g1]]]].L == Lg) {
-            grp.push_back(cj[order[g1]]);
-            gmax = std::max(gmax, pp_[cidx[order[g1]]]);
-            ++g1;
-          }
-          const SvdJob* d_grp = arena.push(grp, s);
-          if (!d_grp) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
-          TT_TRY(certify_batched(s, (int)grp.size(), d_grp, gmax, eps / std::sqrt((double)std::max(Lg - 1, 1)), unit));
-          g0 = g1;
-        }
+        int gmax = 0;
+        for (int a : cidx) gmax = std::max(gmax, pp_[a]);
+        const SvdJob* d_cj = arena.push(cj, s);
+        if (!d_cj) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
+        TT_TRY(certify_batched(s, (int)cj.size(), d_cj, gmax, unit, kMixed ? kMixedSigmaFloor : 0.0));
         TT_TRY(read_ints(R.rank));
         for (int a : cidx) cert[a] = h_int[act[a]] != 0;
       }
@@ -448,16 +436,13 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
         }
       }
       const int ns = (int)sv.size();
-      // jobs grouped by SVD cluster size (one stream per size class) and by train length
-      // (delta_scale = eps / sqrt(L - 1) enters the FP64 skip rule and the truncation)
-      auto run_grouped = [&](const std::vector<int>& qs, bool by_len, bool fp64_kernel, auto&& fn) -> int {
-        std::vector<std::pair<std::pair<int, int>, std::vector<int>>> groups;
+      // jobs grouped by SVD cluster size (one stream per size class)
+      auto run_grouped = [&](const std::vector<int>& qs, bool fp64_kernel, auto&& fn) -> int {
+        std::vector<std::pair<int, std::vector<int>>> groups;
         for (int q : qs) {
           const int cs = svd_cluster_size(pp_[svd_a[q]], fp64_kernel);
-          const int Lq = by_len ? tr[act[svd_a[q]]].L : 0;
-          auto it = std::find_if(groups.begin(), groups.end(),
-                                 [&](const auto& e) { return e.first.first == cs && e.first.second == Lq; });
-          if (it == groups.end()) groups.push_back({{cs, Lq}, {q}});
+          auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& e) { return e.first == cs; });
+          if (it == groups.end()) groups.push_back({cs, {q}});
           else it->second.push_back(q);
         }
         std::vector<const SvdJob*> dptr(groups.size());
@@ -473,9 +458,8 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
         }
         TT_TRY(lanes.fork());
         for (size_t g = 0; g < groups.size(); ++g) {
-          const int cs = groups[g].first.first, Lg = groups[g].first.second;
-          const double ds = by_len ? eps / std::sqrt((double)std::max(Lg - 1, 1)) : 0.0;
-          TT_TRY(fn(lanes.lane(class_of(cs)), (int)groups[g].second.size(), dptr[g], gmax[g], cs, ds));
+          const int cs = groups[g].first;
+          TT_TRY(fn(lanes.lane(class_of(cs)), (int)groups[g].second.size(), dptr[g], gmax[g], cs));
         }
         return lanes.join();
       };
@@ -486,7 +470,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
         const MapJob* d_x32back = arena.push(x32back, s);
         if (!d_conv || !d_x32back) return fail(TT_ERR_WORKSPACE, "tt_apply_round_batched: job arena full");
         TT_TRY((map_batched<double, float>(s, ns, d_conv, mx_pp)));
-        TT_TRY(run_grouped(all_q, false, false, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int cs, double) {
+        TT_TRY(run_grouped(all_q, false, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int cs) {
           return jacobi_f32_batched(ls, g, dg, gm, 30, cs);
         }));
         TT_TRY((map_batched<float, double>(s, ns, d_x32back, mx_pp)));
@@ -501,16 +485,16 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
         }
         tm.fallbacks += (int64_t)fin.size();
         if (!fin.empty())
-          TT_TRY(run_grouped(fin, false, true, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int cs, double) {
-            return jacobi_f64_batched(ls, g, dg, gm, 0.0, 30, cs);
+          TT_TRY(run_grouped(fin, true, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int cs) {
+            return jacobi_f64_batched(ls, g, dg, gm, false, 30, cs);
           }));
       } else {
-        TT_TRY(run_grouped(all_q, true, true, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int cs, double ds) {
-          return jacobi_f64_batched(ls, g, dg, gm, ds, 30, cs);
+        TT_TRY(run_grouped(all_q, true, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int cs) {
+          return jacobi_f64_batched(ls, g, dg, gm, true, 30, cs);
         }));
       }
-      TT_TRY(run_grouped(all_q, true, !kMixed, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int, double ds) {
-        return svd_truncate_batched(ls, g, dg, gm, ds, max_rank, kMixed ? kMixedSigmaFloor : 0.0);
+      TT_TRY(run_grouped(all_q, !kMixed, [&](cudaStream_t ls, int g, const SvdJob* dg, int gm, int) {
+        return svd_truncate_batched(ls, g, dg, gm, max_rank, kMixed ? kMixedSigmaFloor : 0.0);
       }));
       TT_TRY(read_ints(R.rank));
       for (int a : svd_a) {

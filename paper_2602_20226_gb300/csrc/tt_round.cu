@@ -199,11 +199,15 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
       // C_k <- Q and C_{k+1} <- R C_{k+1} represent the same tensor as the SVD factors
       // would (they differ by an orthogonal gauge), and the SVD is skipped.
       bool certified = false;
-      // (the certificate subtracts p u ||R||_F, so it cannot succeed unless p u < delta / ||x||)
-      const double unit = sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+      // (the certificate subtracts p u ||R||_F with u the FP64 unit roundoff of its own
+      // arithmetic, so it cannot succeed unless p u < delta / ||x||; in the mixed form it
+      // certifies the stored FP32 factor, and also sigma_min > 2^-22 ||R||_F, the floor
+      // below which the mixed form drops singular values)
+      const double unit = 2.220446049250313e-16;
+      const double cert_floor = std::is_same<T, float>::value ? kMixedSigmaFloor : 0.0;
       if (tall && (max_rank <= 0 || max_rank >= p) && 64 * (size_t)p <= 200 * 1024 && p * unit < delta_scale) {
         pe = prof.begin();
-        TT_TRY(certify_full_rank(s, B.sv, B.sv.X, p, p, delta_scale, unit));
+        TT_TRY(certify_full_rank(s, B.sv, B.sv.X, p, p, delta_scale, unit, cert_floor));
         prof.end(pe, PROF_CERT, (double)p * p * p / 3.0);
         int flag = 0;
         TT_TRY(read_back(s, B.sv.rank, &flag, sizeof(int)));

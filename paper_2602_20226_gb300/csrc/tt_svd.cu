@@ -562,9 +562,19 @@ __device__ __forceinline__ void svd_truncate_body(
     bool finite = isfinite(nrm);
     double tail2 = 0.0;
     int r = ncol;
+    // sqrt(t) <= delta decided without the square root away from the threshold: with
+    // d2 = delta^2 rounded, t <= d2 (1 - 2^-48) implies sqrt(t) < delta (1 - 2^-50) and
+    // t >= d2 (1 + 2^-48) implies sqrt(t) > delta (1 + 2^-50), beyond the rounding of the
+    // square root either way; in between the square root is taken as before
+    // (delta^2 outside the normal range, where the relative margins do not hold: always
+    // the square root)
+    const double d2 = delta * delta;
+    const bool margins = d2 >= 0x1p-1000 && d2 <= 0x1p+1000;
+    const double d2_lo = margins ? d2 * (1.0 - 0x1p-48) : -1.0, d2_hi = margins ? d2 * (1.0 + 0x1p-48) : INFINITY;
     for (int j = ncol - 1; j >= 1; --j) {
       const double t = fma(srt[j], srt[j], tail2);
-      if (sqrt(t) <= delta) {
+      const bool keep_tail = t <= d2_lo ? true : (t >= d2_hi ? false : sqrt(t) <= delta);
+      if (keep_tail) {
         tail2 = t;
         r = j;
       } else {
@@ -639,9 +649,13 @@ __global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int 
   rinv_colnorm_body(R, p, ldr, colsq, blockIdx.x);
 }
 
-// flag = 1 if 1/||R^{-1}||_F - p u ||R||_F > 1.01 delta (certified full rank), else 0.
+// flag = 1 if 1/||R^{-1}||_F - p u ||R||_F > max(1.01 delta, rel_floor ||R||_F) (certified
+// full rank: sigma_min(R) exceeds both the truncation threshold and the relative floor
+// below which the mixed form drops singular values), else 0.  u is the unit roundoff of
+// the FP64 arithmetic that forms R^{-1} here.
 __device__ __forceinline__ void certify_body(const double* R, int p, int ldr, const double* colsq,
-                                             const double* norm, double delta_scale, double unit, int* flag) {
+                                             const double* norm, double delta_scale, double unit,
+                                             double rel_floor, int* flag) {
   __shared__ double scratch[32];
   double inv2 = 0.0, r2 = 0.0;
   for (int j = threadIdx.x; j < p; j += blockDim.x) inv2 += colsq[j];
@@ -658,14 +672,15 @@ __device__ __forceinline__ void certify_body(const double* R, int p, int ldr, co
     const double delta = delta_scale * (*norm);
     const double lower = (isfinite(inv2) && inv2 > 0.0) ? 1.0 / sqrt(inv2) : 0.0;
     const double slack = (double)p * unit * sqrt(r2);
-    *flag = (lower - slack > 1.01 * delta) ? 1 : 0;
+    *flag = (lower - slack > fmax(1.01 * delta, rel_floor * sqrt(r2))) ? 1 : 0;
   }
 }
 
 __global__ void __launch_bounds__(1024) certify_kernel(const double* R, int p, int ldr,
                                                        const double* colsq, const double* norm,
-                                                       double delta_scale, double unit, int* flag) {
-  certify_body(R, p, ldr, colsq, norm, delta_scale, unit, flag);
+                                                       double delta_scale, double unit, double rel_floor,
+                                                       int* flag) {
+  certify_body(R, p, ldr, colsq, norm, delta_scale, unit, rel_floor, flag);
 }
 
 // ------------------------------------------------------------------ batched forms
@@ -677,17 +692,16 @@ __global__ void __launch_bounds__(256) rinv_colnorm_batched_kernel(const SvdJob*
   rinv_colnorm_body(J.X, J.n, J.ldx, J.sigma, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(1024) certify_batched_kernel(const SvdJob* __restrict__ jobs, double delta_scale,
-                                                               double unit) {
+__global__ void __launch_bounds__(1024) certify_batched_kernel(const SvdJob* __restrict__ jobs, double unit,
+                                                               double rel_floor) {
   const SvdJob& J = jobs[blockIdx.x];
-  certify_body(J.X, J.n, J.ldx, J.sigma, J.norm, delta_scale, unit, J.rank);
+  certify_body(J.X, J.n, J.ldx, J.sigma, J.norm, J.dscale, unit, rel_floor, J.rank);
 }
 
 __global__ void __launch_bounds__(1024) svd_truncate_batched_kernel(const SvdJob* __restrict__ jobs,
-                                                                    double delta_scale, long long max_rank,
-                                                                    double rel_floor) {
+                                                                    long long max_rank, double rel_floor) {
   const SvdJob& J = jobs[blockIdx.x];
-  svd_truncate_body(J.X, J.n, J.n, J.ldx, J.norm, delta_scale, max_rank, rel_floor, J.sigma, J.perm, J.rank,
+  svd_truncate_body(J.X, J.n, J.n, J.ldx, J.norm, J.dscale, max_rank, rel_floor, J.sigma, J.perm, J.rank,
                     J.status);
 }
 
@@ -716,7 +730,7 @@ __device__ __forceinline__ unsigned cluster_sum_u32(unsigned* slot, int cs, unsi
 }
 
 template <int NT, int TPL, int CS>
-__global__ void __launch_bounds__(NT) jacobi_f64_cluster_kernel(const SvdJob* __restrict__ jobs, double delta_scale,
+__global__ void __launch_bounds__(NT) jacobi_f64_cluster_kernel(const SvdJob* __restrict__ jobs, int skip,
                                                                 int max_sweeps) {
   const int rank = (int)(blockIdx.x % CS);
   const SvdJob& J = jobs[blockIdx.x / CS];
@@ -726,7 +740,7 @@ __global__ void __launch_bounds__(NT) jacobi_f64_cluster_kernel(const SvdJob* __
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = rank * NW + warp, GW = CS * NW;
   const double tol = sqrt((double)ncol) * 2.220446049250313e-16;
-  const double nl = delta_scale > 0.0 ? delta_scale * __ldcg(J.norm) / sqrt(2.0 * ncol) : 0.0;
+  const double nl = (skip && J.dscale > 0.0) ? J.dscale * __ldcg(J.norm) / sqrt(2.0 * ncol) : 0.0;
   const double negl = nl * nl;
   const int N = ncol + (ncol & 1), npairs = N / 2;
   __shared__ unsigned s_rot, s_tot;
@@ -1001,7 +1015,7 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
 }
 
 int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale,
-                      double unit) {
+                      double unit, double rel_floor) {
   static int configured = -1;
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
@@ -1014,7 +1028,7 @@ int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ld
   }
   rinv_colnorm_kernel<<<(unsigned)ceil_div(p, 8), 256, smem, s>>>(R, p, ldr, w.sigma);
   TT_LAUNCH_CHECK();
-  certify_kernel<<<1, 1024, 0, s>>>(R, p, ldr, w.sigma, w.norm, delta_scale, unit, w.rank);
+  certify_kernel<<<1, 1024, 0, s>>>(R, p, ldr, w.sigma, w.norm, delta_scale, unit, rel_floor, w.rank);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }
@@ -1102,7 +1116,7 @@ int svd_left_vectors(cudaStream_t s, const SvdWork& w, int nrow, int r, TO* U) {
 }
 
 // ---------------------------------------------------------------- batched launchers
-int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale, double unit) {
+int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double unit, double rel_floor) {
   if (nj <= 0 || n_max <= 0) return TT_OK;
   const size_t smem = 8 * (size_t)n_max * sizeof(double);
   if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "certify_batched: rank too large");
@@ -1116,7 +1130,7 @@ int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, dou
   }
   rinv_colnorm_batched_kernel<<<dim3((unsigned)ceil_div(n_max, 8), (unsigned)nj), 256, smem, s>>>(d_jobs);
   TT_LAUNCH_CHECK();
-  certify_batched_kernel<<<nj, 1024, 0, s>>>(d_jobs, delta_scale, unit);
+  certify_batched_kernel<<<nj, 1024, 0, s>>>(d_jobs, unit, rel_floor);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }
@@ -1149,7 +1163,7 @@ int allow_cluster16(K kernel) {
 }
 
 template <int CS>
-int f64_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale, int max_sweeps) {
+int f64_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int skip, int max_sweeps) {
   if (CS > 8) {
     static int configured = -1;
     int dev = 0;
@@ -1163,13 +1177,13 @@ int f64_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double 
     }
   }
   if (n_max <= 128)
-    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 4, CS>, CS, nj, 256, 0, d_jobs, delta_scale, max_sweeps);
+    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 4, CS>, CS, nj, 256, 0, d_jobs, skip, max_sweeps);
   if (n_max <= 256)
-    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 8, CS>, CS, nj, 256, 0, d_jobs, delta_scale, max_sweeps);
+    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 8, CS>, CS, nj, 256, 0, d_jobs, skip, max_sweeps);
   if (n_max <= 512)
-    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 16, CS>, CS, nj, 256, 0, d_jobs, delta_scale,
+    return launch_cluster(s, jacobi_f64_cluster_kernel<256, 16, CS>, CS, nj, 256, 0, d_jobs, skip,
                           max_sweeps);
-  return launch_cluster(s, jacobi_f64_cluster_kernel<256, 0, CS>, CS, nj, 256, 0, d_jobs, delta_scale, max_sweeps);
+  return launch_cluster(s, jacobi_f64_cluster_kernel<256, 0, CS>, CS, nj, 256, 0, d_jobs, skip, max_sweeps);
 }
 
 template <int CS>
@@ -1208,15 +1222,15 @@ int svd_cluster_size(int n, bool fp64) {
   return 16;
 }
 
-int jacobi_f64_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
+int jacobi_f64_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, bool skip,
                        int max_sweeps, int cs) {
   if (nj <= 0 || n_max <= 0) return TT_OK;
   switch (cs) {
-    case 1: return f64_cluster<1>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
-    case 2: return f64_cluster<2>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
-    case 4: return f64_cluster<4>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
-    case 8: return f64_cluster<8>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
-    case 16: return f64_cluster<16>(s, nj, d_jobs, n_max, delta_scale, max_sweeps);
+    case 1: return f64_cluster<1>(s, nj, d_jobs, n_max, skip ? 1 : 0, max_sweeps);
+    case 2: return f64_cluster<2>(s, nj, d_jobs, n_max, skip ? 1 : 0, max_sweeps);
+    case 4: return f64_cluster<4>(s, nj, d_jobs, n_max, skip ? 1 : 0, max_sweeps);
+    case 8: return f64_cluster<8>(s, nj, d_jobs, n_max, skip ? 1 : 0, max_sweeps);
+    case 16: return f64_cluster<16>(s, nj, d_jobs, n_max, skip ? 1 : 0, max_sweeps);
   }
   return fail(TT_ERR_ARG, "jacobi_f64_batched: cluster size");
 }
@@ -1233,8 +1247,8 @@ int jacobi_f32_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, 
   return fail(TT_ERR_ARG, "jacobi_f32_batched: cluster size");
 }
 
-int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
-                         int64_t max_rank, double rel_floor) {
+int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int64_t max_rank,
+                         double rel_floor) {
   if (nj <= 0 || n_max <= 0) return TT_OK;
   const size_t smem = 2 * (size_t)n_max * sizeof(double);
   if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "svd_truncate_batched: bond rank too large");
@@ -1246,7 +1260,7 @@ int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max
                                        200 * 1024));
     configured = dev;
   }
-  svd_truncate_batched_kernel<<<nj, 1024, smem, s>>>(d_jobs, delta_scale, (long long)max_rank, rel_floor);
+  svd_truncate_batched_kernel<<<nj, 1024, smem, s>>>(d_jobs, (long long)max_rank, rel_floor);
   TT_LAUNCH_CHECK();
   return TT_OK;
 }

@@ -40,11 +40,14 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
                  int64_t max_rank, double rel_floor = 0.0);
 
 // No-truncation certificate for the upper-triangular p x p factor R (FP64, ld ldr):
-// *w.rank <- 1 if sigma_min(R) > delta = delta_scale * (*w.norm) is proven, else 0;
-// `unit` is the unit roundoff R was computed in (the certificate allows p*unit*||R||_F
-// of error in R).  Uses w.sigma as scratch.
+// *w.rank <- 1 if sigma_min(R) > max(1.01 delta, rel_floor ||R||_F), delta =
+// delta_scale * (*w.norm), is proven, else 0.  The bound allows p*unit*||R||_F of error;
+// unit = 2^-53, the certificate's own FP64 arithmetic, in both forms: the FP64 form's R
+// is FP64, and the mixed form truncates on the singular values of its stored FP32 factor
+// (copied exactly into R), so a certificate for that factor is what its SVD step would
+// decide (rel_floor = the mixed form's 2^-22 floor).  Uses w.sigma as scratch.
 int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale,
-                      double unit);
+                      double unit, double rel_floor);
 
 // ---- batched forms (one job per train of a batch, jobs in device memory)
 struct SvdJob {
@@ -60,18 +63,23 @@ struct SvdJob {
   const double* norm;
   int r;            // svd_left_batched: columns to gather into U (n x r)
   void* U;
+  double dscale;    // the train's delta / ||x|| = eps / sqrt(L - 1)
 };
-int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale, double unit);
+// The batched SVD kernels take each job's delta from J.dscale * *J.norm, so trains of
+// different lengths share one launch.
+int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double unit, double rel_floor);
 // Bond SVDs of a batch, one thread-block cluster of cs CTAs per job, all
 // jobs of similar size: svd_cluster_size(n, fp64) picks cs (1 to 16) for bond rank n.
 int svd_cluster_size(int n, bool fp64);
-int jacobi_f64_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
+// skip: leave pairs of two negligible columns alone (each ||x||^2 < delta^2 / (2 n));
+// false rotates every pair (the FP64 finish of the mixed form's FP32 sweeps)
+int jacobi_f64_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, bool skip,
                        int max_sweeps, int cs);
 // FP32 form: rotates J.X32 into W (rotations not accumulated); *sweeps = -1 when a job's
 // FP32 sweeps did not settle (its caller finishes it in FP64).
 int jacobi_f32_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int max_sweeps, int cs);
-int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, double delta_scale,
-                         int64_t max_rank, double rel_floor);
+int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int64_t max_rank,
+                         double rel_floor);
 template <typename TO>
 int svd_left_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int64_t max_elems);
 size_t jacobi_block_smem_gs(int gs, int nrow, int ncol);
