@@ -288,7 +288,7 @@ def run_ours(args):
             "ranks_out_max": max(Z.ranks),
             "mixed": {"value": round(value_mixed, 4), "unit": "GFLOP/s", "ms_per_step": round(ms_mixed, 4),
                       "eps": MIXED_EPS, "fp64_ms_per_step_same_eps": round(ms_fp64_same_eps, 4),
-                      "dtype": "f32 cores, compensated-FP32 (Dot2) GEMMs, FP32 Jacobi with FP64 sigma/truncation/norm",
+                      "dtype": "f32 cores; FP32 GEMMs with better-than-FP32 sums (sliced tensor-core form where its tiles fill the GPU, Dot2 SIMT below); FP64 full-rank certificate, else FP32 Jacobi; FP64 sigma/truncation/norm",
                       "speedup_vs_fp64": round(ms_fp64_same_eps / ms_mixed, 3),
                       "rel_err_vs_fp64_oracle": err_mixed},
             "roofline": roofline,

@@ -56,10 +56,13 @@ typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
 
 /* Arithmetic form of tt_round.
  *   TT_PREC_FP64    everything in FP64 (the plain FP64 GPU form; TT_F64 cores).
- *   TT_PREC_MIXED   TT_F32 cores; QR panels in FP32, the dense core GEMMs on the
- *                   tensor cores in TF32 with a 3-term hi/lo split and FP32
- *                   accumulation; bond SVDs, the truncation decision and the norm
- *                   in FP64. */
+ *   TT_PREC_MIXED   TT_F32 cores; Householder panels in FP32; the QR updates and the
+ *                   core GEMMs with better-than-FP32 sums: on the tensor cores in the
+ *                   sliced form of tt_gemm_f32_sliced (exact tensor-core sums) where its
+ *                   tiles fill the GPU, compensated FP32 dot products below that; a bond
+ *                   whose stored factor an FP64 certificate proves full rank skips its
+ *                   SVD, the others get an FP32 one-sided Jacobi; singular values, the
+ *                   truncation decision and the norm in FP64. */
 typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_prec;
 
 /* Limits of this build. */

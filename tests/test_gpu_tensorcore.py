@@ -10,9 +10,10 @@ allows 4e-7 sqrt(K), far below the ~1e-4 a TF32-only product (lo terms missing) 
 
 Mixed rounding: FP32 cores and FP32 QR panels; the QR updates and the core GEMMs use
 the sliced tensor-core form where its tiles fill the GPU and compensated FP32 dot products
-(Dot2) below that, the bond SVD is an FP32 Jacobi (FP64 Jacobi where it hits its sweep
-cap), and sigma, the truncation and the norm are FP64; compared with the FP64 oracle run
-on the same FP32 values.  Stated tolerances: e <= 1e-6 (the target)
+(Dot2) below that; a bond whose stored factor an FP64 certificate proves full rank skips
+its SVD, the others get an FP32 Jacobi (FP64 Jacobi where it hits its sweep cap); sigma,
+the truncation and the norm are FP64; compared with the FP64 oracle run on the same FP32
+values.  Stated tolerances: e <= 1e-6 (the target)
 for the small and ragged trains and for the norm; for the 40-site rank-320 train at
 eps = 1e-6 both results sit up to 1e-6 from the unrounded train, so their distance is
 allowed 4e-6 (measured 2.0e-6 with equal ranks).  The 3xTF32 GEMM is not on the
