@@ -9,6 +9,7 @@ from .api import (  # noqa: F401
     MPO,
     TT,
     TTError,
+    gemm_f32,
     load,
     tt_apply_mpo,
     tt_apply_mpo_backward,
