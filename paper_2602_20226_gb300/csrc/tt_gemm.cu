@@ -15,7 +15,9 @@
 // second FP32 accumulator.  The result is as accurate as if computed in about twice
 // the working precision and then rounded, at ~10 FP32 operations per multiply-add:
 // several times the throughput of FP64 arithmetic on GB300, whose FP64 rate is about
-// one sixtieth of its FP32 rate.
+// one sixtieth of its FP32 rate.  FP32 products large enough to give every SM a
+// 128 x 64 tile go to the sliced tensor-core form instead (tt_gemm_tc.cu), which is as
+// accurate for these uses and several times faster.
 #include <type_traits>
 
 #include "tt_gemm.cuh"

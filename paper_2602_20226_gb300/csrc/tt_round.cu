@@ -268,7 +268,8 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         TT_TRY(svd_left_vectors<T>(s, B.sv, p, rn, B.vsel));
         if (mixed_svd) {
           // one Newton-Schulz step U <- U (3I - U^T U) / 2 takes the orthogonality defect
-          // eta of the FP32 Jacobi's vectors to O(eta^2) (Dot2 GEMMs keep it accurate)
+          // eta of the FP32 Jacobi's vectors to O(eta^2) (GEMMs with better-than-FP32 sums
+          // keep it accurate)
           float* U = reinterpret_cast<float*>(B.vsel);
           TT_TRY((gemm_core<float>(s, rn, rn, p, 1.0, U, p, 1, U, 1, p, 0.0, B.G32, 1, rn, B.sv.status)));
           TT_TRY(newton_schulz_h(s, B.G32, rn));
