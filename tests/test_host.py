@@ -67,6 +67,37 @@ def test_library_validates_on_host_without_gpu():
     assert lib.tt_round_workspace_size(ctypes.byref(x2), 0) == 0
 
 
+def test_gemm_and_batched_entries_validate_on_host_without_gpu():
+    lib = _abi.load()
+    vp = ctypes.c_void_p
+    for fn in ("tt_gemm_f32_sliced", "tt_gemm_f32"):
+        f = getattr(lib, fn)
+        # negative size
+        assert f(-1, 4, 4, 1.0, vp(1), 4, 1, vp(1), 4, 1, 0.0, vp(1), 4, 1, None) == 1
+        # NULL operand with K > 0
+        assert f(4, 4, 4, 1.0, None, 4, 1, vp(1), 4, 1, 0.0, vp(1), 4, 1, None) == 1
+        assert b"NULL" in lib.tt_last_error()
+        # empty output: nothing to do, no device touched
+        assert f(0, 4, 4, 1.0, None, 4, 1, None, 4, 1, 0.0, None, 4, 1, None) == 0
+    L = 3
+    d = (ctypes.c_int32 * L)(2, 2, 2)
+    r = (ctypes.c_int64 * (L + 1))(1, 2, 2, 1)
+    p = (ctypes.c_void_p * L)(1, 2, 3)
+    a = (ctypes.c_int64 * (L + 1))(1, 3, 3, 1)
+    W = (_abi.tt_mpo * 1)(_abi.tt_mpo(L, _abi.TT_F32, d, a, p))
+    X = (_abi.tt_train * 1)(_abi.tt_train(L, _abi.TT_F32, d, r, p))
+    Y = (_abi.tt_train * 1)(_abi.tt_train(L, _abi.TT_F32, d, (ctypes.c_int64 * (L + 1))(1, 6, 6, 1), p))
+    O = (_abi.tt_train * 1)(_abi.tt_train(L, _abi.TT_F32, d, (ctypes.c_int64 * (L + 1))(1, 6, 6, 1), p))
+    streams = (ctypes.c_void_p * 1)(None)
+    f = lib.tt_apply_round_batched
+    assert f(-1, W, X, Y, 1e-6, 0, _abi.TT_PREC_MIXED, O, vp(1), 1 << 20, streams, 1) == 1
+    assert f(0, None, None, None, 1e-6, 0, _abi.TT_PREC_MIXED, None, None, 0, None, 0) == 0
+    assert f(1, W, X, Y, -1.0, 0, _abi.TT_PREC_MIXED, O, vp(1), 1 << 20, streams, 1) == 1  # eps < 0
+    assert f(1, W, X, Y, 1e-6, 0, 5, O, vp(1), 1 << 20, streams, 1) == 1  # unknown prec
+    assert f(1, W, X, Y, 1e-6, 0, _abi.TT_PREC_FP64, O, vp(1), 1 << 20, streams, 1) == 3  # FP32 cores, FP64 form
+    assert f(1, W, X, Y, 1e-6, 0, _abi.TT_PREC_MIXED, O, None, 1 << 20, streams, 1) != 0  # no workspace
+
+
 @pytest.mark.parametrize("n_dims,bits", [(1, 7), (2, 4), (3, 3), (2, 5)])
 def test_laplacian_constructor_matches_oracle(n_dims, bits):
     a = qtt.laplacian_mpo(n_dims, bits)
