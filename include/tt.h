@@ -56,7 +56,8 @@ typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
 
 /* Arithmetic form of tt_round.
  *   TT_PREC_FP64    everything in FP64 (the plain FP64 GPU form; TT_F64 cores).
- *   TT_PREC_MIXED   TT_F32 cores; Householder panels in FP32; the QR updates and the
+ *   TT_PREC_MIXED   TT_F32 cores; Householder panels in FP32 (tt_round), or factored
+ *                   in FP64 and rounded to FP32 (tt_apply_round_batched); the QR updates and the
  *                   core GEMMs with better-than-FP32 sums: on the tensor cores in the
  *                   sliced form of tt_gemm_f32_sliced (exact tensor-core sums) where its
  *                   tiles fill the GPU, compensated FP32 dot products below that; a bond

@@ -58,7 +58,8 @@ int64_t max_y_rank(int32_t n, const tt_mpo* W, const tt_train* x) {
 size_t arena_bytes(int32_t n, int64_t r_max, int nb) {
   const size_t panels = (size_t)ceil_div(r_max, nb) + 1;
   // QR and thin Q: three update GEMMs per panel each
-  return align_up((1u << 20) + (size_t)n * (6 * panels * sizeof(GemmJob<double, double, double>) + 8192));
+  return align_up((1u << 20) + (size_t)n * (6 * panels * sizeof(GemmJob<double, double, double>) +
+                                            panels * (5 * sizeof(MapJob) + sizeof(QrJob<double>)) + 8192));
 }
 
 // results the host reads after each step, contiguous so that one copy returns them
@@ -278,7 +279,8 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
       Bufs<T>& B = S.B;
       cin.push_back(copy_job<T>(S.slot[k], B.A, (int64_t)m * nn));
       mx_in = std::max<int64_t>(mx_in, (int64_t)m * nn);
-      qj.push_back(QrJob<T>{B.A, m, nn, m, B.qr.tau, B.qr.tmat, B.qr.vbuf, m, B.qr.w1, B.qr.w2, S.slot[k], m});
+      qj.push_back(QrJob<T>{B.A, m, nn, m, B.qr.tau, B.qr.tmat, B.qr.vbuf, m, B.qr.w1, B.qr.w2, S.slot[k], m,
+                                  B.p64, B.v64, B.t64, B.tau64});
       rext.push_back(MapJob{B.A, B.Rbuf, pp, nn, 1, m, 1, pp, MAP_UPPER});
       mx_r = std::max<int64_t>(mx_r, (int64_t)pp * nn);
       const int rows = (int)S.cur[k - 1] * S.d[k - 1];
@@ -345,13 +347,15 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
       tall[a] = m >= nn;
       if (tall[a]) {
         cin.push_back(MapJob{S.slot[k], B.A, m, nn, nn, 1, 1, m, MAP_COPY});  // row-major -> column-major
-        qj_tall.push_back(QrJob<T>{B.A, m, nn, m, B.qr.tau, B.qr.tmat, B.qr.vbuf, m, B.qr.w1, B.qr.w2, B.Q, m});
+        qj_tall.push_back(QrJob<T>{B.A, m, nn, m, B.qr.tau, B.qr.tmat, B.qr.vbuf, m, B.qr.w1, B.qr.w2, B.Q, m,
+                                       B.p64, B.v64, B.t64, B.tau64});
         tall_idx.push_back(a);
         rext.push_back(MapJob{B.A, B.Rbuf, pp, nn, 1, m, 1, pp, MAP_UPPER});
         xext.push_back(MapJob{B.A, B.sv.X, pp, nn, 1, m, 1, pp, MAP_UPPER});
       } else {
         cin.push_back(copy_job<T>(S.slot[k], B.A, (int64_t)m * nn));  // C_k^T column-major (nn x m)
-        qj_wide.push_back(QrJob<T>{B.A, nn, m, nn, B.qr.tau, B.qr.tmat, B.qr.vbuf, nn, B.qr.w1, B.qr.w2, B.Q, nn});
+        qj_wide.push_back(QrJob<T>{B.A, nn, m, nn, B.qr.tau, B.qr.tmat, B.qr.vbuf, nn, B.qr.w1, B.qr.w2, B.Q, nn,
+                                       B.p64, B.v64, B.t64, B.tau64});
         wide_idx.push_back(a);
         // X = R^T (m x m): R = upper m x m of the QR'd (nn x m) matrix
         xext.push_back(MapJob{B.A, B.sv.X, m, m, 1, nn, m, 1, MAP_UPPER});

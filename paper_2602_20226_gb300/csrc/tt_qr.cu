@@ -13,6 +13,9 @@
 // the form: FP64 SIMT, or tensor cores for FP32).
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
+#include "tt_kernels.cuh"
 #include "tt_qr.cuh"
 
 namespace cg = cooperative_groups;
@@ -614,6 +617,52 @@ int build_panel_gemms(cudaStream_t s, const std::vector<QrJob<T>>& hj, int nb, b
   return TT_OK;
 }
 
+// FP32 jobs with FP64 scratch: the panel at column j0 of every job copied into its FP64
+// scratch (rows j0..m-1 as rows 0..mr-1), factored there by the FP64 panel kernel, and
+// R, the reflectors, T and tau written back rounded to FP32.  The FP32 panel's own
+// arithmetic (reflectors formed and applied in FP32 inside the panel) left the mixed
+// form ~2e-6 from the unrounded trains; with FP64 panels it stays below 1e-6, while the
+// trailing updates remain in the FP32 GEMMs (sliced tensor-core form or Dot2).
+int panel_f64(cudaStream_t s, const std::vector<QrJob<float>>& hj, int j0, int nb, JobArena& arena) {
+  std::vector<MapJob> to64, back;
+  std::vector<QrJob<double>> dj;
+  int64_t mx = 1;
+  int mr_max = 0;
+  for (const auto& J : hj) {
+    const int p = std::min(J.m, J.n);
+    if (j0 >= p) continue;
+    const int jb = std::min(nb, p - j0), mr = J.m - j0;
+    float* Ablk = J.A + j0 + (int64_t)j0 * J.lda;
+    to64.push_back(MapJob{Ablk, J.p64, mr, jb, 1, J.lda, 1, mr, MAP_COPY});
+    QrJob<double> D{};
+    D.A = J.p64;
+    D.m = mr;
+    D.n = jb;
+    D.lda = mr;
+    D.tau = J.tau64;
+    D.tmat = J.t64;
+    D.vbuf = J.v64;
+    D.ldv = mr;
+    dj.push_back(D);
+    back.push_back(MapJob{J.p64, Ablk, mr, jb, 1, mr, 1, J.lda, MAP_COPY});
+    back.push_back(MapJob{J.v64, J.vbuf + j0 + (int64_t)j0 * J.ldv, mr, jb, 1, mr, 1, J.ldv, MAP_COPY});
+    back.push_back(MapJob{J.t64, J.tmat + (int64_t)(j0 / nb) * nb * nb, jb, jb, 1, nb, 1, nb, MAP_COPY});
+    back.push_back(MapJob{J.tau64, J.tau + j0, jb, 1, 1, jb, 1, jb, MAP_COPY});
+    mx = std::max<int64_t>(mx, (int64_t)mr * jb);
+    mr_max = std::max(mr_max, mr);
+  }
+  if (dj.empty()) return TT_OK;
+  const MapJob* d_to = arena.push(to64, s);
+  const MapJob* d_back = arena.push(back, s);
+  const QrJob<double>* d_dj = arena.push(dj, s);
+  if (!d_to || !d_back || !d_dj) return fail(TT_ERR_WORKSPACE, "batched QR: job arena full");
+  TT_TRY((map_batched<float, double>(s, (int)to64.size(), d_to, mx)));
+  const size_t smem = std::min(kPanelSmem, (size_t)mr_max * nb * sizeof(double));
+  qr_panel_batched_kernel<double, 512><<<(unsigned)dj.size(), 512, smem, s>>>(d_dj, 0, nb, smem);
+  TT_LAUNCH_CHECK();
+  return map_batched<double, float>(s, (int)back.size(), d_back, mx);
+}
+
 template <typename T>
 int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, const QrJob<T>* d_jobs, int nb,
                            JobArena& arena, unsigned* status) {
@@ -626,8 +675,12 @@ int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, cons
   if (configured[sizeof(T) == 8] != dev) {
     TT_CUDA_CHECK(cudaFuncSetAttribute(qr_panel_batched_kernel<T, 512>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
+    TT_CUDA_CHECK(cudaFuncSetAttribute(qr_panel_batched_kernel<double, 512>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
     configured[sizeof(T) == 8] = dev;
   }
+  bool f64_panels = false;
+  if constexpr (std::is_same<T, float>::value) f64_panels = hj[0].p64 != nullptr;
   int p_max = 0, m_max = 0;
   for (const auto& J : hj) {
     p_max = std::max(p_max, std::min(J.m, J.n));
@@ -639,6 +692,13 @@ int householder_qr_batched(cudaStream_t s, const std::vector<QrJob<T>>& hj, cons
   TT_TRY(build_panel_gemms(s, hj, nb, false, npanels, arena, meta, D));
   for (int pn = 0; pn < npanels; ++pn) {
     const int j0 = pn * nb;
+    if constexpr (std::is_same<T, float>::value) {
+      if (f64_panels) {
+        TT_TRY(panel_f64(s, hj, j0, nb, arena));
+        TT_TRY(apply_panels(s, d_jobs, nj, nb, false, pn, D.d1, D.d2, D.d3, D.e1, D.e2, D.e3, meta, status));
+        continue;
+      }
+    }
     const size_t smem = std::min(kPanelSmem, (size_t)(m_max - j0) * nb * sizeof(T));
     qr_panel_batched_kernel<T, 512><<<nj, 512, smem, s>>>(d_jobs, j0, nb, smem);
     TT_LAUNCH_CHECK();

@@ -45,6 +45,13 @@ struct QrJob {
   T* w2;    // [nb * max(n, min(m, n))]
   T* Q;     // form_thin_q_batched: m x min(m, n), ld ldq
   int ldq;
+  // FP32 jobs: FP64 scratch of one panel (rows x nb, ld rows), its reflectors (same),
+  // T factor (nb x nb) and tau (nb).  When set, every panel is factored in FP64 and
+  // written back rounded to FP32; the trailing updates stay in the FP32 GEMMs.
+  double* p64 = nullptr;
+  double* v64 = nullptr;
+  double* t64 = nullptr;
+  double* tau64 = nullptr;
 };
 
 // hj: the jobs on the host (sizes, for the launch shapes and the update GEMMs);

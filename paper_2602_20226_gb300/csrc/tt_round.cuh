@@ -29,6 +29,7 @@ struct Dims {
   int L = 0;
   int64_t S_max = 1;  // largest core (elements)
   int64_t r_max = 1;  // largest rank
+  int64_t d_max = 1;  // largest mode
 };
 
 inline Dims dims_of(const tt_train* x) {
@@ -37,6 +38,7 @@ inline Dims dims_of(const tt_train* x) {
   for (int k = 0; k < x->L; ++k) {
     D.S_max = std::max<int64_t>(D.S_max, x->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1]);
     D.r_max = std::max<int64_t>(D.r_max, std::max(x->ranks[k], x->ranks[k + 1]));
+    D.d_max = std::max<int64_t>(D.d_max, x->d[k]);
   }
   return D;
 }
@@ -45,6 +47,9 @@ template <typename T>
 struct Bufs {
   T *A = nullptr, *Q = nullptr, *tmp = nullptr, *Rbuf = nullptr, *vsel = nullptr, *F = nullptr;
   float *X32 = nullptr, *G32 = nullptr;  // mixed-form bond SVD: FP32 factor, Newton-Schulz Gram
+  // mixed form, batched driver: FP64 scratch of one Householder panel (the FP32 QRs factor
+  // each panel in FP64 and round R, the reflectors, T and tau back to FP32)
+  double *p64 = nullptr, *v64 = nullptr, *t64 = nullptr, *tau64 = nullptr;
   QrWork<T> qr;
   SvdWork sv;
 };
@@ -67,6 +72,11 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   if (std::is_same<T, float>::value) {
     B.X32 = c.take<float>((size_t)D.r_max * D.r_max);
     B.G32 = c.take<float>((size_t)D.r_max * D.r_max);
+    const size_t rows = (size_t)(D.d_max * D.r_max);  // rows of any QR of the sweeps
+    B.p64 = c.take<double>(rows * nb);
+    B.v64 = c.take<double>(rows * nb);
+    B.t64 = c.take<double>((size_t)nb * nb);
+    B.tau64 = c.take<double>((size_t)nb);
   }
   B.sv.sigma = c.take<double>(D.r_max);
   B.sv.perm = c.take<int>(D.r_max);
