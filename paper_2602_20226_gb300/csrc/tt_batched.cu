@@ -43,7 +43,7 @@ size_t train_slice_bytes(const tt_mpo& W, const tt_train& x, int32_t prec) {
   std::vector<int64_t> r = y_ranks(W, x);
   tt_train y = x;
   y.ranks = r.data();
-  return align_up(round_workspace_bytes(&y, prec));
+  return align_up(round_workspace_bytes(&y, prec, true));
 }
 
 int64_t max_y_rank(int32_t n, const tt_mpo* W, const tt_train* x) {
@@ -212,7 +212,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
     tt_train yi = x[i];
     yi.ranks = S.cur.data();
     Carver c(p);
-    carve(c, dims_of(&yi), nb, S.B);
+    carve(c, dims_of(&yi), nb, S.B, true);
     // the host-read words of every train live in the contiguous result arrays
     S.B.sv.rank = R.rank + i;
     S.B.sv.sweeps = R.sweeps + i;
@@ -280,7 +280,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
       cin.push_back(copy_job<T>(S.slot[k], B.A, (int64_t)m * nn));
       mx_in = std::max<int64_t>(mx_in, (int64_t)m * nn);
       qj.push_back(QrJob<T>{B.A, m, nn, m, B.qr.tau, B.qr.tmat, B.qr.vbuf, m, B.qr.w1, B.qr.w2, S.slot[k], m,
-                                  B.p64, B.v64, B.t64, B.tau64});
+                                  B.qr.tmat64, B.w1d, B.w2d});
       rext.push_back(MapJob{B.A, B.Rbuf, pp, nn, 1, m, 1, pp, MAP_UPPER});
       mx_r = std::max<int64_t>(mx_r, (int64_t)pp * nn);
       const int rows = (int)S.cur[k - 1] * S.d[k - 1];
@@ -348,14 +348,14 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
       if (tall[a]) {
         cin.push_back(MapJob{S.slot[k], B.A, m, nn, nn, 1, 1, m, MAP_COPY});  // row-major -> column-major
         qj_tall.push_back(QrJob<T>{B.A, m, nn, m, B.qr.tau, B.qr.tmat, B.qr.vbuf, m, B.qr.w1, B.qr.w2, B.Q, m,
-                                       B.p64, B.v64, B.t64, B.tau64});
+                                       B.qr.tmat64, B.w1d, B.w2d});
         tall_idx.push_back(a);
         rext.push_back(MapJob{B.A, B.Rbuf, pp, nn, 1, m, 1, pp, MAP_UPPER});
         xext.push_back(MapJob{B.A, B.sv.X, pp, nn, 1, m, 1, pp, MAP_UPPER});
       } else {
         cin.push_back(copy_job<T>(S.slot[k], B.A, (int64_t)m * nn));  // C_k^T column-major (nn x m)
         qj_wide.push_back(QrJob<T>{B.A, nn, m, nn, B.qr.tau, B.qr.tmat, B.qr.vbuf, nn, B.qr.w1, B.qr.w2, B.Q, nn,
-                                       B.p64, B.v64, B.t64, B.tau64});
+                                       B.qr.tmat64, B.w1d, B.w2d});
         wide_idx.push_back(a);
         // X = R^T (m x m): R = upper m x m of the QR'd (nn x m) matrix
         xext.push_back(MapJob{B.A, B.sv.X, m, m, 1, nn, m, 1, MAP_UPPER});

@@ -35,13 +35,19 @@ __device__ __forceinline__ void gemm_tile(int M, int N, int K, double alpha, con
                                           int64_t sam, int64_t sak, const TB* __restrict__ B, int64_t sbk,
                                           int64_t sbn, double beta, TC* __restrict__ C, int64_t scm,
                                           int64_t scn, int bx, int by) {
-  // FP32 operands and output: compensated FP32 (Dot2); anything else in FP64
-  constexpr bool kAllF32 = std::is_same<TA, float>::value && std::is_same<TB, float>::value &&
-                          std::is_same<TC, float>::value;
-  constexpr bool kDot2 = COMP && kAllF32;
-  using Acc = std::conditional_t<kAllF32, float, double>;  // FP32 operands: FP32 (plain or Dot2)
+  // FP32 A and B: compensated FP32 (Dot2) into an FP32 or FP64 C (plain FP32 sums if !COMP
+  // and C is FP32).  FP32 A, FP64 B, FP32 C (the mixed form's update X -= V W2 with W2 in
+  // FP64): Dot2 with B split into hi + lo FP32 words, a b = a b_hi (exact TwoProduct) +
+  // a b_lo.  Every other combination in FP64.
+  constexpr bool kF32AB = std::is_same<TA, float>::value && std::is_same<TB, float>::value;
+  constexpr bool kAllF32 = kF32AB && std::is_same<TC, float>::value;
+  constexpr bool kSplitB = COMP && std::is_same<TA, float>::value && std::is_same<TB, double>::value &&
+                           std::is_same<TC, float>::value;
+  constexpr bool kDot2 = COMP && (kF32AB || kSplitB);
+  using Acc = std::conditional_t<(kAllF32 || kDot2), float, double>;
   __shared__ Acc As[BK][BM + 1];
   __shared__ Acc Bs[BK][BN + 1];
+  __shared__ Acc Bl[kSplitB ? BK : 1][kSplitB ? BN + 1 : 1];  // low words of B (kSplitB)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = by * BM, n0 = bx * BN;
@@ -84,25 +90,38 @@ __device__ __forceinline__ void gemm_tile(int M, int N, int K, double alpha, con
         nn = e / BK;
       }
       const int gn = n0 + nn, gk = k0 + kk;
-      Acc v = Acc(0);
-      if (gn < N && gk < K) v = (Acc)B[(int64_t)gk * sbk + (int64_t)gn * sbn];
-      Bs[kk][nn] = v;
+      if constexpr (kSplitB) {
+        double v = 0.0;
+        if (gn < N && gk < K) v = (double)B[(int64_t)gk * sbk + (int64_t)gn * sbn];
+        const float h = (float)v;
+        Bs[kk][nn] = h;
+        Bl[kk][nn] = (float)(v - (double)h);
+      } else {
+        Acc v = Acc(0);
+        if (gn < N && gk < K) v = (Acc)B[(int64_t)gk * sbk + (int64_t)gn * sbn];
+        Bs[kk][nn] = v;
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      Acc a[TM], b[TN];
+      Acc a[TM], b[TN], bl[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) {
+        b[j] = Bs[kk][tx + 16 * j];
+        if constexpr (kSplitB) bl[j] = Bl[kk][tx + 16 * j];
+        else bl[j] = Acc(0);
+      }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
           if constexpr (kDot2) {
             const float p = __fmul_rn(a[i], b[j]);
-            const float e = __fmaf_rn(a[i], b[j], -p);  // a b = p + e exactly
+            float e = __fmaf_rn(a[i], b[j], -p);  // a b = p + e exactly
+            if constexpr (kSplitB) e = __fmaf_rn(a[i], bl[j], e);
             const float x = acc[i][j];
             const float t = __fadd_rn(x, p);  // TwoSum: x + p = t + f exactly
             const float z = __fsub_rn(t, x);

@@ -14,6 +14,8 @@ struct QrWork {
   int nb = 16;       // panel width (<= 32)
   T* tau = nullptr;  // [>= min(m, n)]
   T* tmat = nullptr; // [npanels][nb][nb] T factors (column-major)
+  double* tmat64 = nullptr;  // FP32 matrices: the T factors in FP64 (recomputed from the
+                             // FP32-rounded reflectors), [npanels][nb][nb]
   T* vbuf = nullptr; // explicit Householder vectors, column-major, ld = ldv >= m
   int ldv = 0;
   T* w1 = nullptr;   // [nb * ncols]
@@ -45,13 +47,12 @@ struct QrJob {
   T* w2;    // [nb * max(n, min(m, n))]
   T* Q;     // form_thin_q_batched: m x min(m, n), ld ldq
   int ldq;
-  // FP32 jobs: FP64 scratch of one panel (rows x nb, ld rows), its reflectors (same),
-  // T factor (nb x nb) and tau (nb).  When set, every panel is factored in FP64 and
-  // written back rounded to FP32; the trailing updates stay in the FP32 GEMMs.
-  double* p64 = nullptr;
-  double* v64 = nullptr;
-  double* t64 = nullptr;
-  double* tau64 = nullptr;
+  // FP32 jobs (the mixed form): the T factors in FP64, [panel][nb][nb], recomputed from the
+  // FP32-rounded reflectors by the FP64 panel kernel, and W1 = V^T X, W2 = op(T) W1 in FP64
+  // ([nb * max(n, min(m, n))] each) for the updates X -= V W2.
+  double* tmat64 = nullptr;
+  double* w1d = nullptr;
+  double* w2d = nullptr;
 };
 
 // hj: the jobs on the host (sizes, for the launch shapes and the update GEMMs);

@@ -102,15 +102,15 @@ int read_back(cudaStream_t s, const void* dev, void* host, size_t bytes) {
 
 }  // namespace
 
-size_t round_workspace_bytes(const tt_train* x, int prec) {
+size_t round_workspace_bytes(const tt_train* x, int prec, bool batched) {
   const Dims D = dims_of(x);
   Carver c(nullptr);
   if (prec == TT_PREC_FP64) {
     Bufs<double> B;
-    return carve(c, D, panel_width<double>(), B);
+    return carve(c, D, panel_width<double>(), B, batched);
   }
   Bufs<float> B;
-  return carve(c, D, panel_width<float>(), B);
+  return carve(c, D, panel_width<float>(), B, batched);
 }
 
 template <typename T>

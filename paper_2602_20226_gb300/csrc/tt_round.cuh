@@ -47,15 +47,16 @@ template <typename T>
 struct Bufs {
   T *A = nullptr, *Q = nullptr, *tmp = nullptr, *Rbuf = nullptr, *vsel = nullptr, *F = nullptr;
   float *X32 = nullptr, *G32 = nullptr;  // mixed-form bond SVD: FP32 factor, Newton-Schulz Gram
-  // mixed form, batched driver: FP64 scratch of one Householder panel (the FP32 QRs factor
-  // each panel in FP64 and round R, the reflectors, T and tau back to FP32)
-  double *p64 = nullptr, *v64 = nullptr, *t64 = nullptr, *tau64 = nullptr;
+  // mixed form: W1 = V^T X and W2 = op(T) W1 of the batched driver's QR updates, in FP64
+  double *w1d = nullptr, *w2d = nullptr;
   QrWork<T> qr;
   SvdWork sv;
 };
 
+// batched: the scratch of a train of tt_apply_round_batched (the FP64 W buffers of the
+// mixed form's batched QR updates; tt_round's own updates need none)
 template <typename T>
-size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
+size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B, bool batched = false) {
   B.A = c.take<T>(D.S_max);
   B.Q = c.take<T>(D.S_max);
   B.tmp = c.take<T>(D.S_max);
@@ -63,6 +64,7 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   B.qr.vbuf = c.take<T>(D.S_max);
   B.qr.tau = c.take<T>(D.r_max + 32);
   B.qr.tmat = c.take<T>((size_t)nb * nb * (ceil_div(D.r_max, nb) + 1));
+  if (std::is_same<T, float>::value) B.qr.tmat64 = c.take<double>((size_t)nb * nb * (ceil_div(D.r_max, nb) + 1));
   B.qr.w1 = c.take<T>((size_t)nb * D.r_max);
   B.qr.w2 = c.take<T>((size_t)nb * D.r_max);
   B.Rbuf = c.take<T>((size_t)D.r_max * D.r_max);
@@ -72,11 +74,10 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B) {
   if (std::is_same<T, float>::value) {
     B.X32 = c.take<float>((size_t)D.r_max * D.r_max);
     B.G32 = c.take<float>((size_t)D.r_max * D.r_max);
-    const size_t rows = (size_t)(D.d_max * D.r_max);  // rows of any QR of the sweeps
-    B.p64 = c.take<double>(rows * nb);
-    B.v64 = c.take<double>(rows * nb);
-    B.t64 = c.take<double>((size_t)nb * nb);
-    B.tau64 = c.take<double>((size_t)nb);
+    if (batched) {
+      B.w1d = c.take<double>((size_t)nb * D.r_max);
+      B.w2d = c.take<double>((size_t)nb * D.r_max);
+    }
   }
   B.sv.sigma = c.take<double>(D.r_max);
   B.sv.perm = c.take<int>(D.r_max);
@@ -110,7 +111,7 @@ struct RoundStats {
   int jacobi_sweeps = 0;
 };
 
-size_t round_workspace_bytes(const tt_train* x, int prec);
+size_t round_workspace_bytes(const tt_train* x, int prec, bool batched = false);
 
 template <typename T>
 int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, double* norm_out,
