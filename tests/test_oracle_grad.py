@@ -125,3 +125,59 @@ def test_inner_vjp_brute_force():
         e[k][idx] = 1.0
         g[idx] = np.sum(core.full(e) * fy)
     assert np.allclose(g, dx[k], rtol=1e-12, atol=1e-14)
+
+
+# ---- the adjoint of rounding (Section 3.2's sweeps, reversed)
+
+
+def _gap_train(seed, L):
+    """A train with a clear gap in every unfolding spectrum: a rank-3 part plus 1e-5 times a
+    rank-2 part (bond ranks 5, none above the ranks of the unfoldings)."""
+    big = inputs.random_tt(seed, L, 2, [1, 2] + [3] * (L - 3) + [2, 1])
+    small = inputs.random_tt(seed + 1, L, 2, [1] + [2] * (L - 1) + [1])
+    return core.add(big, core.scale(small, 1e-5))
+
+
+def test_round_vjp_without_truncation_is_the_inner_gradient():
+    """No truncation: round(x) = x as a tensor, so the gradient of <round(x), y> is that of
+    <x, y> (a closed form independent of the rounding's gauge)."""
+    for L, ranks in [(4, [1, 2, 3, 2, 1]), (8, [1, 2, 4, 8, 9, 8, 4, 2, 1]), (6, [1, 2, 4, 3, 4, 2, 1])]:
+        x = inputs.random_tt(11 + L, L, 2, ranks)
+        y = inputs.random_tt(12 + L, L, 2, 3)
+        dout, _ = grad.inner_vjp(core.round_tt(x, 1e-14), y)
+        dx = grad.round_vjp(x, 1e-14, dout)
+        ref, _ = grad.inner_vjp(x, y)
+        scale = max(np.abs(r).max() for r in ref)
+        for a, b in zip(dx, ref):
+            assert np.abs(a - b).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-8])
+def test_round_vjp_fd(eps):
+    """<round(x), y> with truncation (eps = 1e-3 drops the 1e-5 part: ranks 5 -> 3) and
+    without (eps = 1e-8), against central differences."""
+    L = 7
+    x = _gap_train(21, L)
+    y = inputs.random_tt(23, L, 2, 3)
+    out = core.round_tt(x, eps)
+    assert max(core.ranks(out)) == (3 if eps == 1e-3 else 5)
+    dout, _ = grad.inner_vjp(out, y)
+    dx = grad.round_vjp(x, eps, dout)
+    _fd_check(lambda: core.inner(core.round_tt(x, eps), y), x, dx)
+
+
+def test_round_vjp_fd_norm_loss():
+    """A second loss, ||round(x) - b||^2 for a fixed train b, through the same adjoint."""
+    L = 6
+    x = _gap_train(31, L)
+    b = inputs.random_tt(33, L, 2, 2)
+
+    def loss():
+        z = core.round_tt(x, 1e-3)
+        return core.inner(z, z) - 2.0 * core.inner(z, b)
+
+    z = core.round_tt(x, 1e-3)
+    d1, d2 = grad.inner_vjp(z, z)
+    d3, _ = grad.inner_vjp(z, b, -2.0)
+    dout = [p + q + r for p, q, r in zip(d1, d2, d3)]
+    _fd_check(loss, x, grad.round_vjp(x, 1e-3, dout))
