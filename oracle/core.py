@@ -144,11 +144,13 @@ def scale(x, alpha):
 def inner(x, y):
     """<x, y> with every index contracted ('i,i->'), by the left environment sweep.
 
-    E_0 = 1, E_k = sum_i X_k(i)^T E_{k-1} Y_k(i); <x, y> = E_L.
+    E_0 = 1, E_k = sum_i X_k(i)^T E_{k-1} Y_k(i); <x, y> = E_L.  The three-factor sum is
+    contracted pairwise (optimize=True: O(r^3) per site instead of the O(r^4) of a joint loop
+    over all five indices).
     """
     e = np.ones((1, 1))
     for xk, yk in zip(x, y):
-        e = np.einsum("ab,aic,bid->cd", e, xk, yk)
+        e = np.einsum("ab,aic,bid->cd", e, xk, yk, optimize=True)
     return float(e[0, 0])
 
 

@@ -52,16 +52,16 @@ def inner_vjp(x, y, dout=1.0):
     L = len(x)
     left = [np.ones((1, 1))]
     for k in range(L):
-        left.append(np.einsum("ab,aic,bid->cd", left[-1], x[k], y[k]))
+        left.append(np.einsum("ab,aic,bid->cd", left[-1], x[k], y[k], optimize=True))
     right = [None] * (L + 1)
     right[L] = np.ones((1, 1))
     for k in range(L - 1, -1, -1):
-        right[k] = np.einsum("aic,cd,bid->ab", x[k], right[k + 1], y[k])
+        right[k] = np.einsum("aic,cd,bid->ab", x[k], right[k + 1], y[k], optimize=True)
     dx, dy = [], []
     for k in range(L):
         el, er = left[k], right[k + 1]
-        dx.append(dout * np.einsum("ab,bid,cd->aic", el, y[k], er))
-        dy.append(dout * np.einsum("ab,aic,cd->bid", el, x[k], er))
+        dx.append(dout * np.einsum("ab,bid,cd->aic", el, y[k], er, optimize=True))
+        dy.append(dout * np.einsum("ab,aic,cd->bid", el, x[k], er, optimize=True))
     return dx, dy
 
 
