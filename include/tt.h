@@ -56,13 +56,15 @@ typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
 
 /* Arithmetic form of tt_round.
  *   TT_PREC_FP64    everything in FP64 (the plain FP64 GPU form; TT_F64 cores).
- *   TT_PREC_MIXED   TT_F32 cores; Householder panels in FP32 (tt_round), or factored
- *                   in FP64 and rounded to FP32 (tt_apply_round_batched); the QR updates and the
- *                   core GEMMs with better-than-FP32 sums: on the tensor cores in the
- *                   sliced form of tt_gemm_f32_sliced (exact tensor-core sums) where its
- *                   tiles fill the GPU, compensated FP32 dot products below that; a bond
- *                   whose stored factor an FP64 certificate proves full rank skips its
- *                   SVD, the others get an FP32 one-sided Jacobi; singular values, the
+ *   TT_PREC_MIXED   TT_F32 cores.  Every Householder panel is factored in FP64 and rounded
+ *                   to FP32, with tau and the T factor recomputed in FP64 from the rounded
+ *                   reflectors; the block-reflector updates keep W1 = V^T X and W2 = T^T W1
+ *                   in FP64 and sum V W2 with exact products in float-float (compensated
+ *                   FP32 arithmetic), rounding X once; the core GEMMs run on the tensor
+ *                   cores in the sliced form of tt_gemm_f32_sliced (exact tensor-core sums)
+ *                   where its tiles fill the GPU, compensated FP32 dot products below that;
+ *                   a bond whose stored factor an FP64 certificate proves full rank skips
+ *                   its SVD, the others get an FP32 one-sided Jacobi; singular values, the
  *                   truncation decision and the norm in FP64. */
 typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_prec;
 
@@ -134,6 +136,27 @@ size_t tt_round_workspace_size(const tt_train* x, int32_t prec);
 int tt_round(const tt_train* x, double eps, int64_t max_rank, int32_t prec, tt_train* out,
              double* norm_out, void* workspace, size_t ws_bytes, void* stream);
 
+/* Device workspace (bytes) that tt_round_backward needs for input x. */
+size_t tt_round_backward_workspace_size(const tt_train* x);
+
+/* Adjoint of tt_round in the FP64 form (Section 3.2's two sweeps, reversed):
+ *   dx += d loss / dx, given dout = d loss / d out for out = tt_round(x, eps, max_rank,
+ *   TT_PREC_FP64).
+ * The forward rounding is run again (the same arithmetic as tt_round, so the same output
+ * cores and gauge), recording its factors; then the left-to-right bonds are reversed (thin-QR
+ * adjoint for the bonds the full-rank certificate kept, the adjoint of the leading left
+ * singular vectors for the truncated ones, near-degenerate kept pairs guarded) and the
+ * right-to-left steps (thin-QR adjoints).
+ *   x      TT_F64 input of the rounding; dout TT_F64 with the ranks of out; dx TT_F64 with x's
+ *          ranks, accumulated (+=).
+ * The derivative exists where the truncation ranks are locally constant (a gap at every cut)
+ * and every right-to-left factor has full rank, i.e. no bond rank of x exceeds the rank of
+ * its unfolding; TT_ERR_NUMERIC (non-finite gradient) otherwise.  The loss should not depend
+ * on the gauge of out's cores (e.g. a function of the represented tensor).  TT_ERR_SHAPE if
+ * dout's ranks differ from round(x)'s.  Synchronises the stream. */
+int tt_round_backward(const tt_train* x, double eps, int64_t max_rank, const tt_train* dout, tt_train* dx,
+                      void* workspace, size_t ws_bytes, void* stream);
+
 /* ---- batched apply + round over many independent trains ---- */
 
 /* Device workspace (bytes) for tt_apply_round_batched: one rounding workspace per train
@@ -179,7 +202,9 @@ int tt_inner(const tt_train* x, const tt_train* y, double* out, void* workspace,
  *   loads the library until the process exits.  Trains whose tt_inner_workspace_size
  *   exceeds 4 MiB are rejected with TT_ERR_UNSUPPORTED before anything is launched.
  *   Set-up: the first call on each device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   that device current); make that first call before any stream capture.  The address
+ *   is kept for the life of the process: after cudaDeviceReset (or anything else that
+ *   destroys the device's primary context) later calls on that device are invalid.
  *   Sharing: all calls on a device use the same array and it keeps the last call's
  *   contents, so calls that overlap on the GPU (other streams, other threads) race;
  *   serialise them.  Synchronises the stream like tt_inner. */
@@ -223,6 +248,14 @@ int tt_eval_backward(const tt_train* x, const uint8_t* digits, int64_t n, const 
 
 /* ---- diagnostics ---- */
 
+/* Exercises the library's bounded device-side wait (the wait of the dataflow Jacobi SVDs)
+ * on a flag that nothing sets: the wait gives up after poll_limit polls, raises the timeout
+ * bit of a device status word and the kernel returns; the call then returns TT_ERR_TIMEOUT
+ * and the CUDA context stays usable.  scratch: caller-allocated device memory of at least
+ * 12 bytes (zeroed by the call).  poll_limit in [1, 2^24] (the library's own limit), else
+ * TT_ERR_ARG.  Synchronises the stream.  No counterpart in the paper (failure handling). */
+int tt_debug_wait_expiry(int64_t poll_limit, void* scratch, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far (all
  * threads, all devices).  A caller reads it before and after a region of work to
  * count the launches inside it. */
@@ -239,6 +272,13 @@ uint64_t tt_launch_count(void);
  * tt_profile_read returns TT_ERR_ARG for an unknown class. */
 void tt_profile_enable(int32_t on);
 int tt_profile_read(int32_t cls, double* ms, double* nominal_flops, uint64_t* count);
+
+/* Executed work of a profiler class since tt_profile_enable(1), where it differs from the
+ * nominal count: for class 0 the Jacobi sweeps that actually ran, 6 p^3 flops per sweep of a
+ * p x p factor (every pair of columns: three dot products and one rotation of length p);
+ * bonds whose SVD the full-rank certificate skipped contribute nothing.  The other classes
+ * equal their nominal flops.  TT_ERR_ARG for an unknown class. */
+int tt_profile_read_executed(int32_t cls, double* executed_flops);
 
 /* C = alpha A B + beta C in FP32 on the tensor cores: TF32 with a 3-term hi/lo split
  * (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation).  Not on the rounding path: the

@@ -8,6 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libtt.so")
 
 TT_OK = 0
+TT_ERR_ARG, TT_ERR_SHAPE, TT_ERR_DTYPE, TT_ERR_UNSUPPORTED = 1, 2, 3, 4
+TT_ERR_WORKSPACE, TT_ERR_CUDA, TT_ERR_NUMERIC, TT_ERR_TIMEOUT = 5, 6, 7, 8
 STATUS_NAMES = {
     0: "TT_OK",
     1: "TT_ERR_ARG",
@@ -55,6 +57,10 @@ SIGNATURES = {
     "tt_launch_count": (ctypes.c_uint64, []),
     "tt_profile_enable": (None, [i32]),
     "tt_profile_read": (ctypes.c_int, [i32, P(f64), P(f64), P(ctypes.c_uint64)]),
+    "tt_profile_read_executed": (ctypes.c_int, [i32, P(f64)]),
+    "tt_debug_wait_expiry": (ctypes.c_int, [i64, vp, vp]),
+    "tt_round_backward_workspace_size": (sz, [P(tt_train)]),
+    "tt_round_backward": (ctypes.c_int, [P(tt_train), f64, i64, P(tt_train), P(tt_train), vp, sz, vp]),
     "tt_apply_mpo": (ctypes.c_int, [P(tt_mpo), P(tt_train), P(tt_train), vp]),
     "tt_hadamard": (ctypes.c_int, [P(tt_train), P(tt_train), P(tt_train), vp]),
     "tt_round_workspace_size": (sz, [P(tt_train), i32]),

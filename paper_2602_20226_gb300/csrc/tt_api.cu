@@ -26,17 +26,18 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 namespace {
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;
-double g_prof_ms[PROF_CLASSES] = {0}, g_prof_flops[PROF_CLASSES] = {0};
+double g_prof_ms[PROF_CLASSES] = {0}, g_prof_flops[PROF_CLASSES] = {0}, g_prof_exec[PROF_CLASSES] = {0};
 uint64_t g_prof_n[PROF_CLASSES] = {0};
 }  // namespace
 
 bool profile_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
 
-void profile_add(int cls, double ms, double flops) {
+void profile_add(int cls, double ms, double flops, double executed) {
   if (cls < 0 || cls >= PROF_CLASSES) return;
   std::lock_guard<std::mutex> g(g_prof_mu);
   g_prof_ms[cls] += ms;
   g_prof_flops[cls] += flops;
+  g_prof_exec[cls] += executed;
   g_prof_n[cls] += 1;
 }
 
@@ -244,7 +245,7 @@ uint64_t tt_launch_count(void) { return g_launches.load(std::memory_order_relaxe
 
 void tt_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> g(g_prof_mu);
-  for (int c = 0; c < PROF_CLASSES; ++c) g_prof_ms[c] = g_prof_flops[c] = 0.0, g_prof_n[c] = 0;
+  for (int c = 0; c < PROF_CLASSES; ++c) g_prof_ms[c] = g_prof_flops[c] = g_prof_exec[c] = 0.0, g_prof_n[c] = 0;
   g_prof_on.store(on != 0);
 }
 
@@ -254,6 +255,13 @@ int tt_profile_read(int32_t cls, double* ms, double* nominal_flops, uint64_t* co
   if (ms) *ms = g_prof_ms[cls];
   if (nominal_flops) *nominal_flops = g_prof_flops[cls];
   if (count) *count = g_prof_n[cls];
+  return TT_OK;
+}
+
+int tt_profile_read_executed(int32_t cls, double* executed_flops) {
+  if (cls < 0 || cls >= PROF_CLASSES) return fail(TT_ERR_ARG, "tt_profile_read_executed: bad class");
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (executed_flops) *executed_flops = g_prof_exec[cls];
   return TT_OK;
 }
 
@@ -314,6 +322,30 @@ int tt_round(const tt_train* x, double eps, int64_t max_rank, int32_t prec, tt_t
     if (prec == TT_PREC_FP64)
       return round_impl<double>(x, eps, max_rank, out, norm_out, workspace, ws_bytes, as_stream(stream), nullptr);
     return round_impl<float>(x, eps, max_rank, out, norm_out, workspace, ws_bytes, as_stream(stream), nullptr);
+  });
+}
+
+size_t tt_round_backward_workspace_size(const tt_train* x) {
+  if (check_train(x, "x") != TT_OK) return 0;
+  return round_backward_workspace_bytes(x);
+}
+
+int tt_round_backward(const tt_train* x, double eps, int64_t max_rank, const tt_train* dout, tt_train* dx,
+                      void* workspace, size_t ws_bytes, void* stream) {
+  return guarded([&]() -> int {
+    TT_TRY(check_train(x, "x"));
+    TT_TRY(check_train(dout, "dout"));
+    TT_TRY(check_train(dx, "dx"));
+    if (x->dtype != TT_F64 || dout->dtype != TT_F64 || dx->dtype != TT_F64)
+      return fail(TT_ERR_DTYPE, "tt_round_backward: x, dout and dx must be TT_F64 (the FP64 form)");
+    TT_TRY(check_same_modes(dout, x->d, x->L, "dout"));
+    TT_TRY(check_same_modes(dx, x->d, x->L, "dx"));
+    for (int k = 0; k <= x->L; ++k)
+      if (dx->ranks[k] != x->ranks[k]) return fail(TT_ERR_SHAPE, "tt_round_backward: dx must have x's ranks");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(TT_ERR_ARG, "tt_round_backward: eps must be finite and >= 0");
+    if (!workspace) return fail(TT_ERR_WORKSPACE, "tt_round_backward: workspace is NULL");
+    g_last_error.clear();
+    return round_backward_impl(x, eps, max_rank, dout, dx, workspace, ws_bytes, as_stream(stream));
   });
 }
 

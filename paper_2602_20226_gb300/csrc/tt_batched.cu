@@ -18,6 +18,7 @@
 // oracle) - half the memory traffic of the V-accumulating form (8.5 s instead of 14 s of
 // bond SVDs for the 512-train batch).
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
@@ -593,10 +594,14 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
   }
   // ---- 4. ranks out, status words
   std::vector<unsigned> st(n);
+  std::vector<double> nrm(n);
   TT_CUDA_CHECK(cudaMemcpyAsync(st.data(), R.status, (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  TT_CUDA_CHECK(cudaMemcpyAsync(nrm.data(), R.norm, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
   TT_CUDA_CHECK(cudaStreamSynchronize(s));
   for (int i = 0; i < n; ++i) {
     for (int k = 0; k <= tr[i].L; ++k) out[i].ranks[k] = tr[i].cur[k];
+    if (!std::isfinite(nrm[i]))
+      return fail(TT_ERR_NUMERIC, "tt_apply_round_batched: train " + std::to_string(i) + ": non-finite norm");
     if (st[i] & ST_NONFINITE) return fail(TT_ERR_NUMERIC, "tt_apply_round_batched: train " + std::to_string(i) + ": non-finite values");
     if (st[i] & ST_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_apply_round_batched: device wait expired");
     if (st[i] & ST_NONCONVERGED)

@@ -22,7 +22,7 @@ void note_launch();  // counts kernel launches made by the library (tt_launch_co
 // opt-in event profiler of tt_round's phases (tt_profile_enable / tt_profile_read)
 enum ProfClass { PROF_JACOBI = 0, PROF_QR = 1, PROF_GEMM = 2, PROF_CERT = 3, PROF_CLASSES = 4 };
 bool profile_enabled();
-void profile_add(int cls, double ms, double flops);
+void profile_add(int cls, double ms, double flops, double executed);
 
 #define TT_CUDA_CHECK(expr)                                                             \
   do {                                                                                  \
@@ -126,6 +126,33 @@ __device__ __forceinline__ T block_sum(T v, T* scratch) {
   T t = (lane < nwarps) ? scratch[lane] : T(0);
   t = warp_sum(t);
   return t;
+}
+
+// --------------------------------------------------------------- bounded waits
+// Acquire load of a device word written by another CTA.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Polls until *word >= target.  After `limit` polls it raises ST_TIMEOUT in *status and
+// returns false; it also gives up (false) once another thread has raised ST_TIMEOUT.
+constexpr long long kWaitPolls = 1ll << 24;
+__device__ __forceinline__ bool bounded_wait_ge(const unsigned* word, unsigned target, unsigned* status,
+                                                long long limit = kWaitPolls) {
+  long long polls = 0;
+  while (ld_acquire_u32(word) < target) {
+    if (++polls > limit) {
+      atomicOr(status, (unsigned)ST_TIMEOUT);
+      return false;
+    }
+    if ((polls & 255) == 0 && (*(volatile unsigned*)status & ST_TIMEOUT)) return false;
+  }
+  return true;
 }
 
 // ------------------------------------------------------- bounded grid barrier

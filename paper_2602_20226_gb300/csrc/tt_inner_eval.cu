@@ -8,6 +8,7 @@
 // v = G_1[:, i_1, :] ... G_k[:, i_k, :] in shared memory (column-per-thread, so
 // accesses are conflict-free); the cores are read through the read-only cache
 // where a warp's lanes share at most d distinct rows per load.
+#include <type_traits>
 #include <vector>
 
 #include "tt_gemm.cuh"
@@ -52,6 +53,89 @@ __global__ void eval_kernel(EvalParams<T> P, const uint8_t* __restrict__ digits,
         for (int t = 0; t < JB; ++t)
           if (t < jn) acc[t] = fma(v, __ldg(grow + t), acc[t]);
       }
+#pragma unroll
+      for (int t = 0; t < JB; ++t)
+        if (t < jn) nxt[(size_t)(j0 + t) * S + tid] = acc[t];
+    }
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  if (active) values[smp] = cur[tid];
+}
+
+// Staged form (used when a core fits in shared memory next to the row buffers): per site the
+// CTA copies G_k once into shared memory (rows (a, i) padded to a multiple of 16 bytes plus
+// 16 bytes, so the d digit slices of a row start in different banks), and every thread forms
+// its sample's next row vector from vector loads of the staged core: one 16-byte shared load
+// feeds 4 (FP32) or 2 (FP64) FMAs, where the direct form issued one global load per FMA.
+// The CTA's digits are staged once (S x L contiguous bytes).
+template <typename T>
+__host__ __device__ constexpr int eval_row_pad(int r1) {
+  return sizeof(T) == 4 ? ((r1 + 3) & ~3) + 4 : ((r1 + 1) & ~1) + 2;
+}
+
+template <typename T, int JB>
+__global__ void eval_staged_kernel(EvalParams<T> P, const uint8_t* __restrict__ digits, long long n,
+                                   T* __restrict__ values, unsigned* status, int stage_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = blockDim.x;
+  const int tid = threadIdx.x;
+  T* cur = reinterpret_cast<T*>(smem_raw);
+  T* nxt = cur + (size_t)P.rmax * S;
+  T* stage = nxt + (size_t)P.rmax * S;
+  uint8_t* dg = reinterpret_cast<uint8_t*>(stage + stage_elems + JB);
+  const long long s0 = (long long)blockIdx.x * S;
+  const long long smp = s0 + tid;
+  const bool active = smp < n;
+  {
+    const long long nb = (long long)min((long long)S, n - s0) * P.L;
+    const uint8_t* src = digits + s0 * P.L;
+    for (long long e = tid; e < nb; e += S) dg[e] = src[e];
+  }
+  cur[tid] = T(1);
+  constexpr int VW = 16 / sizeof(T);  // elements per 16-byte load
+  using V = std::conditional_t<sizeof(T) == 4, float4, double2>;
+  for (int k = 0; k < P.L; ++k) {
+    const int r0 = P.r[k], r1 = P.r[k + 1], d = P.d[k];
+    const int r1p = eval_row_pad<T>(r1);
+    __syncthreads();  // the previous site is done with the stage; digits are staged
+    {
+      const T* G = P.g[k];
+      const int rows = r0 * d;
+      for (int e = tid; e < rows * r1; e += S) {
+        const int row = e / r1, c = e - row * r1;
+        stage[row * r1p + c] = G[e];
+      }
+    }
+    __syncthreads();
+    int dig = active ? (int)dg[tid * P.L + k] : 0;
+    if (dig >= d) {
+      if (status) atomicOr(status, (unsigned)ST_BAD_INDEX);
+      dig = 0;
+    }
+    for (int j0 = 0; j0 < r1; j0 += JB) {
+      T acc[JB];
+#pragma unroll
+      for (int t = 0; t < JB; ++t) acc[t] = T(0);
+      for (int a = 0; a < r0; ++a) {
+        const T v = cur[(size_t)a * S + tid];
+        const V* g = reinterpret_cast<const V*>(stage + (size_t)(a * d + dig) * r1p + j0);
+#pragma unroll
+        for (int q = 0; q < JB / VW; ++q) {
+          const V w = g[q];
+          if constexpr (VW == 4) {
+            acc[4 * q + 0] = fma(v, w.x, acc[4 * q + 0]);
+            acc[4 * q + 1] = fma(v, w.y, acc[4 * q + 1]);
+            acc[4 * q + 2] = fma(v, w.z, acc[4 * q + 2]);
+            acc[4 * q + 3] = fma(v, w.w, acc[4 * q + 3]);
+          } else {
+            acc[2 * q + 0] = fma(v, w.x, acc[2 * q + 0]);
+            acc[2 * q + 1] = fma(v, w.y, acc[2 * q + 1]);
+          }
+        }
+      }
+      const int jn = min(JB, r1 - j0);
 #pragma unroll
       for (int t = 0; t < JB; ++t)
         if (t < jn) nxt[(size_t)(j0 + t) * S + tid] = acc[t];
@@ -123,18 +207,26 @@ __global__ void add_into_kernel(const double* src, long long n, T* dst) {
 }  // namespace
 
 // ------------------------------------------------------------------ inner
+// The adjoint keeps the left environments only at every c-th site (c = ceil(sqrt(L))) and
+// recomputes those of one segment at a time during the right-to-left sweep: O(sqrt(L))
+// environments in memory instead of L, for one extra left sweep of GEMMs.
+inline int env_segment(int L) {
+  int c = 1;
+  while (c * c < L) ++c;
+  return c;
+}
+
 size_t inner_workspace_bytes(const tt_train* x, const tt_train* y) {
-  int64_t env = 1, tb = 1, envsum = 0;
-  for (int k = 0; k <= x->L; ++k) {
-    env = std::max<int64_t>(env, x->ranks[k] * y->ranks[k]);
-    envsum += x->ranks[k] * y->ranks[k];
-  }
+  int64_t env = 1, tb = 1;
+  for (int k = 0; k <= x->L; ++k) env = std::max<int64_t>(env, x->ranks[k] * y->ranks[k]);
   for (int k = 0; k < x->L; ++k) {
     tb = std::max<int64_t>(tb, x->ranks[k] * (int64_t)x->d[k] * y->ranks[k + 1]);
     tb = std::max<int64_t>(tb, y->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1]);
   }
-  // forward: 2 env + 1 T; backward: all left envs + 2 right envs + 3 T buffers
-  return (size_t)(envsum + 2 * env + 3 * tb + 64) * sizeof(double) + 1024;
+  const int c = env_segment(x->L);
+  const int64_t ncp = (x->L + c - 1) / c;
+  // forward: 2 env + 1 T; backward: checkpoints + one segment of left envs + 2 right envs + 3 T
+  return (size_t)((ncp + c + 2) * env + 3 * tb + 64) * sizeof(double) + 1024;
 }
 
 template <typename TX, typename TY>
@@ -173,64 +265,78 @@ int inner_backward_impl(const tt_train* x, const tt_train* y, double dout, tt_tr
   if (ws_bytes < inner_workspace_bytes(x, y)) return fail(TT_ERR_WORKSPACE, "tt_inner_backward: workspace too small");
   const int L = x->L;
   int64_t env = 1, tb = 1;
-  std::vector<int64_t> eoff(L + 1);
-  int64_t off = 0;
-  for (int k = 0; k <= L; ++k) {
-    env = std::max<int64_t>(env, x->ranks[k] * y->ranks[k]);
-    eoff[k] = off;
-    off += x->ranks[k] * y->ranks[k];
-  }
+  for (int k = 0; k <= L; ++k) env = std::max<int64_t>(env, x->ranks[k] * y->ranks[k]);
   for (int k = 0; k < L; ++k) {
     tb = std::max<int64_t>(tb, x->ranks[k] * (int64_t)x->d[k] * y->ranks[k + 1]);
     tb = std::max<int64_t>(tb, y->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1]);
   }
-  double* EL = static_cast<double*>(ws);
-  double* ER = EL + off;
+  const int c = env_segment(L);
+  const int ncp = (L + c - 1) / c;
+  double* CP = static_cast<double*>(ws);   // checkpoints: E^L at sites 0, c, 2c, ... (env each)
+  double* SEG = CP + (int64_t)ncp * env;   // the current segment's left environments
+  double* ER = SEG + (int64_t)c * env;
   double* ER2 = ER + env;
   double* T1 = ER2 + env;
   double* T2 = T1 + tb;
   double* T3 = T2 + tb;
-  // left environments E^L_0..E^L_{L-1}
-  set_scalar_kernel<<<1, 1, 0, s>>>(EL, 1.0);
-  TT_LAUNCH_CHECK();
-  for (int k = 0; k < L - 1; ++k) {
+  // E^L_{k+1} from E^L_k (both FP64, rx x ry row-major)
+  auto left_step = [&](int k, const double* El, double* Eout) -> int {
     const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
     const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
     const TX* X = static_cast<const TX*>(x->cores[k]);
     const TY* Y = static_cast<const TY*>(y->cores[k]);
-    TT_TRY((gemm<double, TY, double>(s, rx0, d * ry1, ry0, 1.0, EL + eoff[k], ry0, 1, Y,
-                                     (int64_t)d * ry1, 1, 0.0, T1, (int64_t)d * ry1, 1)));
-    TT_TRY((gemm<TX, double, double>(s, rx1, ry1, rx0 * d, 1.0, X, 1, rx1, T1, ry1, 1, 0.0,
-                                     EL + eoff[k + 1], ry1, 1)));
+    TT_TRY((gemm<double, TY, double>(s, rx0, d * ry1, ry0, 1.0, El, ry0, 1, Y, (int64_t)d * ry1, 1, 0.0, T1,
+                                     (int64_t)d * ry1, 1)));
+    return gemm<TX, double, double>(s, rx1, ry1, rx0 * d, 1.0, X, 1, rx1, T1, ry1, 1, 0.0, Eout, ry1, 1);
+  };
+  // forward: checkpoints only (the segment buffer holds the running environment)
+  set_scalar_kernel<<<1, 1, 0, s>>>(CP, 1.0);
+  TT_LAUNCH_CHECK();
+  {
+    double* run = CP;
+    for (int k = 0; k < L - 1; ++k) {
+      const bool cp = (k + 1) % c == 0;
+      double* dst = cp ? CP + (int64_t)((k + 1) / c) * env : SEG + (int64_t)((k + 1) & 1) * env;
+      TT_TRY(left_step(k, run, dst));
+      run = dst;
+    }
   }
   set_scalar_kernel<<<1, 1, 0, s>>>(ER, 1.0);
   TT_LAUNCH_CHECK();
-  for (int k = L - 1; k >= 0; --k) {
-    const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
-    const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
-    const TX* X = static_cast<const TX*>(x->cores[k]);
-    const TY* Y = static_cast<const TY*>(y->cores[k]);
-    const double* El = EL + eoff[k];
-    if (dx && dx->cores[k]) {
-      // T1 = E^L Y ; dX' ((rx0 d) x rx1) += dout T1' ((rx0 d) x ry1) (E^R)^T (ry1 x rx1)
-      TT_TRY((gemm<double, TY, double>(s, rx0, d * ry1, ry0, 1.0, El, ry0, 1, Y, (int64_t)d * ry1, 1,
-                                       0.0, T1, (int64_t)d * ry1, 1)));
-      TT_TRY((gemm<double, double, TX>(s, rx0 * d, rx1, ry1, dout, T1, ry1, 1, ER, 1, ry1, 1.0,
-                                       static_cast<TX*>(dx->cores[k]), rx1, 1)));
-    }
-    if (dy && dy->cores[k]) {
-      // T2 = (E^L)^T X  (ry0 x d rx1) ; dY' ((ry0 d) x ry1) += dout T2' ((ry0 d) x rx1) E^R
-      TT_TRY((gemm<double, TX, double>(s, ry0, d * rx1, rx0, 1.0, El, 1, ry0, X, (int64_t)d * rx1, 1,
-                                       0.0, T2, (int64_t)d * rx1, 1)));
-      TT_TRY((gemm<double, double, TY>(s, ry0 * d, ry1, rx1, dout, T2, rx1, 1, ER, ry1, 1, 1.0,
-                                       static_cast<TY*>(dy->cores[k]), ry1, 1)));
-    }
-    if (k > 0) {
-      // T3 ((rx0 d) x ry1) = X' E^R ; E^R_new (rx0 x ry0) = T3'' (rx0 x d ry1) Y''^T
-      TT_TRY((gemm<TX, double, double>(s, rx0 * d, ry1, rx1, 1.0, X, rx1, 1, ER, ry1, 1, 0.0, T3, ry1, 1)));
-      TT_TRY((gemm<double, TY, double>(s, rx0, ry0, d * ry1, 1.0, T3, (int64_t)d * ry1, 1, Y, 1,
-                                       (int64_t)d * ry1, 0.0, ER2, ry0, 1)));
-      std::swap(ER, ER2);
+  for (int seg = ncp - 1; seg >= 0; --seg) {
+    const int k0 = seg * c, k1 = std::min(L, k0 + c);
+    // E^L_{k0} .. E^L_{k1 - 1} of this segment into SEG[0 .. k1 - k0)
+    TT_CUDA_CHECK(cudaMemcpyAsync(SEG, CP + (int64_t)seg * env,
+                                  (size_t)x->ranks[k0] * y->ranks[k0] * sizeof(double), cudaMemcpyDeviceToDevice,
+                                  s));
+    for (int k = k0; k + 1 < k1; ++k) TT_TRY(left_step(k, SEG + (int64_t)(k - k0) * env, SEG + (int64_t)(k + 1 - k0) * env));
+    for (int k = k1 - 1; k >= k0; --k) {
+      const int rx0 = (int)x->ranks[k], rx1 = (int)x->ranks[k + 1];
+      const int ry0 = (int)y->ranks[k], ry1 = (int)y->ranks[k + 1], d = x->d[k];
+      const TX* X = static_cast<const TX*>(x->cores[k]);
+      const TY* Y = static_cast<const TY*>(y->cores[k]);
+      const double* El = SEG + (int64_t)(k - k0) * env;
+      if (dx && dx->cores[k]) {
+        // T1 = E^L Y ; dX' ((rx0 d) x rx1) += dout T1' ((rx0 d) x ry1) (E^R)^T (ry1 x rx1)
+        TT_TRY((gemm<double, TY, double>(s, rx0, d * ry1, ry0, 1.0, El, ry0, 1, Y, (int64_t)d * ry1, 1,
+                                         0.0, T1, (int64_t)d * ry1, 1)));
+        TT_TRY((gemm<double, double, TX>(s, rx0 * d, rx1, ry1, dout, T1, ry1, 1, ER, 1, ry1, 1.0,
+                                         static_cast<TX*>(dx->cores[k]), rx1, 1)));
+      }
+      if (dy && dy->cores[k]) {
+        // T2 = (E^L)^T X  (ry0 x d rx1) ; dY' ((ry0 d) x ry1) += dout T2' ((ry0 d) x rx1) E^R
+        TT_TRY((gemm<double, TX, double>(s, ry0, d * rx1, rx0, 1.0, El, 1, ry0, X, (int64_t)d * rx1, 1,
+                                         0.0, T2, (int64_t)d * rx1, 1)));
+        TT_TRY((gemm<double, double, TY>(s, ry0 * d, ry1, rx1, dout, T2, rx1, 1, ER, ry1, 1, 1.0,
+                                         static_cast<TY*>(dy->cores[k]), ry1, 1)));
+      }
+      if (k > 0) {
+        // T3 ((rx0 d) x ry1) = X' E^R ; E^R_new (rx0 x ry0) = T3'' (rx0 x d ry1) Y''^T
+        TT_TRY((gemm<TX, double, double>(s, rx0 * d, ry1, rx1, 1.0, X, rx1, 1, ER, ry1, 1, 0.0, T3, ry1, 1)));
+        TT_TRY((gemm<double, TY, double>(s, rx0, ry0, d * ry1, 1.0, T3, (int64_t)d * ry1, 1, Y, 1,
+                                         (int64_t)d * ry1, 0.0, ER2, ry0, 1)));
+        std::swap(ER, ER2);
+      }
     }
   }
   return TT_OK;
@@ -251,6 +357,31 @@ int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values,
     P.rmax = std::max<int>(P.rmax, (int)x->ranks[k]);
   }
   P.r[x->L] = (int)x->ranks[x->L];
+  // staged form: rows of 2 x rmax x S values, the largest padded core and the digits
+  {
+    int stage = 1;
+    for (int k = 0; k < x->L; ++k)
+      stage = std::max(stage, P.r[k] * P.d[k] * eval_row_pad<T>(P.r[k + 1]));
+    constexpr int SS = 128, JB = 16;
+    const size_t bytes = (2 * (size_t)P.rmax * SS + stage + JB) * sizeof(T) + (size_t)SS * x->L + 16;
+    if (bytes <= 110 * 1024) {
+      static int configured_s[2] = {-1, -1};
+      int dev = 0;
+      TT_CUDA_CHECK(cudaGetDevice(&dev));
+      const int which = sizeof(T) == 8 ? 0 : 1;
+      if (configured_s[which] != dev) {
+        TT_CUDA_CHECK(cudaFuncSetAttribute(eval_staged_kernel<T, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           110 * 1024));
+        configured_s[which] = dev;
+      }
+      const long long blocks = ceil_div(n, SS);
+      if (blocks > 0x7fffffffLL) return fail(TT_ERR_UNSUPPORTED, "tt_eval: too many samples");
+      eval_staged_kernel<T, JB><<<(unsigned)blocks, SS, bytes, s>>>(P, digits, n, static_cast<T*>(values),
+                                                                    status_dev, stage);
+      TT_LAUNCH_CHECK();
+      return TT_OK;
+    }
+  }
   int S = 128;
   auto smem_for = [&](int SS) { return 2 * (size_t)P.rmax * SS * sizeof(T); };
   while (S > 32 && smem_for(S) > 200 * 1024) S /= 2;

@@ -111,11 +111,51 @@ struct RoundStats {
   int jacobi_sweeps = 0;
 };
 
+// Intermediates of one FP64 rounding, recorded for its adjoint (tt_round_backward): device
+// copies in a caller-given arena, host sizes alongside.  All matrices FP64; "cm" = column-major.
+struct RoundRecord {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  bool overflow = false;
+  struct RL {     // right-to-left step at site k: dt = D_k^T (m x n cm) = q r
+    int m = 0, n = 0, p = 0, rows_prev = 0;
+    double *dt = nullptr, *q = nullptr, *r = nullptr;  // q: m x p cm, r: p x n cm
+    double* xprev = nullptr;                           // core k-1 before the step (rows_prev x n)
+  };
+  struct LR {     // left-to-right bond k: a = C_k (m x n row-major) before the bond
+    int m = 0, n = 0, p = 0, rn = 0, cols_next = 0;
+    bool tall = true, cert = false;
+    double *a = nullptr, *q = nullptr, *r = nullptr;     // tall: q (m x p cm), r (p x n cm)
+    double *u = nullptr, *sigma = nullptr, *f = nullptr;  // SVD bonds: U of the square factor
+                                                          // (p x p cm, sorted), sigma (p), F (rn x n)
+    double* next = nullptr;                               // C_{k+1} before the bond (n x cols_next)
+  };
+  std::vector<RL> rl;
+  std::vector<LR> lr;
+  double* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    if (off + n * sizeof(double) > cap) {
+      overflow = true;
+      return nullptr;
+    }
+    double* p = reinterpret_cast<double*>(base + off);
+    off += n * sizeof(double);
+    return p;
+  }
+};
+// arena bytes that recording the rounding of x needs (an upper bound)
+size_t round_record_bytes(const tt_train* x);
+
 size_t round_workspace_bytes(const tt_train* x, int prec, bool batched = false);
 
 template <typename T>
 int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, double* norm_out,
-               void* ws, size_t ws_bytes, cudaStream_t s, RoundStats* stats);
+               void* ws, size_t ws_bytes, cudaStream_t s, RoundStats* stats, RoundRecord* rec = nullptr);
+
+// adjoint of the FP64 rounding (tt_round_bwd.cu)
+size_t round_backward_workspace_bytes(const tt_train* x);
+int round_backward_impl(const tt_train* x, double eps, int64_t max_rank, const tt_train* dout, tt_train* dx,
+                        void* ws, size_t ws_bytes, cudaStream_t s);
 
 size_t batched_workspace_bytes(int32_t n, const tt_mpo* W, const tt_train* x, int32_t prec);
 int apply_round_batched(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, double eps,

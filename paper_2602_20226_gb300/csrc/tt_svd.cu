@@ -91,26 +91,9 @@ __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __r
 }
 
 // Epoch handshake of the dataflow ordering: column c has been through epoch[c] rounds.
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Lane 0 waits (bounded) until column c has finished round t-1, i.e. epoch[c] >= t.
 __device__ __forceinline__ bool wait_column(const unsigned* epoch, int c, unsigned t, unsigned* status) {
-  long long polls = 0;
-  while (ld_acquire_u32(epoch + c) < t) {
-    if (++polls > (1ll << 24)) {
-      atomicOr(status, (unsigned)ST_TIMEOUT);
-      return false;
-    }
-    if ((polls & 255) == 0 && (*(volatile unsigned*)status & ST_TIMEOUT)) return false;
-  }
-  return true;
+  return bounded_wait_ge(epoch + c, t, status);
 }
 
 // FLOW = false: a grid barrier after every round (p - 1 per sweep).
@@ -544,12 +527,17 @@ __device__ __forceinline__ void svd_truncate_body(
     if (lane == 0) sig[c] = sqrt(s);
   }
   __syncthreads();
+  // rank by counting under a total order: NaN sorts last (key -inf) and ties go by index, so
+  // the ranks form a permutation whatever the values (perm indexes columns later; a NaN
+  // compared false both ways and left duplicate ranks and unset entries)
   for (int j = tid; j < ncol; j += blockDim.x) {
     const double sj = sig[j];
+    const double kj = isnan(sj) ? -INFINITY : sj;
     int r = 0;
     for (int q = 0; q < ncol; ++q) {
       const double sq = sig[q];
-      r += (sq > sj) || (sq == sj && q < j);
+      const double kq = isnan(sq) ? -INFINITY : sq;
+      r += (kq > kj) || (kq == kj && q < j);
     }
     perm[r] = j;
     srt[r] = sj;
@@ -610,7 +598,8 @@ __global__ void svd_left_kernel(const double* X, int nrow, int ldx, const int* p
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % nrow), t = (int)(e / nrow);
     const double sg = sig_sorted[t];
-    U[e] = (sg > 0.0) ? (TO)(__ldcg(X + i + (int64_t)perm[t] * ldx) / sg) : TO(0);
+    const int c = perm[t];  // a column of the square factor; out of range only by a bug: zero
+    U[e] = (sg > 0.0 && (unsigned)c < (unsigned)nrow) ? (TO)(__ldcg(X + i + (int64_t)c * ldx) / sg) : TO(0);
   }
 }
 
@@ -898,7 +887,8 @@ __global__ void svd_left_batched_kernel(const SvdJob* __restrict__ jobs) {
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % nrow), t = (int)(e / nrow);
     const double sg = J.sigma[t];
-    U[e] = sg > 0.0 ? (TO)(__ldcg(J.X + i + (int64_t)J.perm[t] * J.ldx) / sg) : TO(0);
+    const int c = J.perm[t];
+    U[e] = (sg > 0.0 && (unsigned)c < (unsigned)nrow) ? (TO)(__ldcg(J.X + i + (int64_t)c * J.ldx) / sg) : TO(0);
   }
 }
 
