@@ -21,5 +21,6 @@ from .api import (  # noqa: F401
     tt_inner,
     tt_inner_backward,
     tt_round,
+    tt_round_backward,
     tt_round_workspace_size,
 )

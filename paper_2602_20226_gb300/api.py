@@ -277,6 +277,20 @@ def tt_inner_backward(x: TT, y: TT, dout: float = 1.0, want_x=True, want_y=True,
     return gx, gy
 
 
+def tt_round_backward(x: TT, eps: float, dout: TT, max_rank: int = 0, stream=None) -> TT:
+    """Gradient w.r.t. the cores of x of a loss of tt_round(x, eps, max_rank) (FP64 form),
+    given its gradient dout w.r.t. the rounded cores (fresh zero-initialised result)."""
+    lib = load()
+    gx = x.zeros_like()
+    a, b, c = _desc(x), _desc(dout), _desc(gx)
+    need = int(lib.tt_round_backward_workspace_size(a.ref()))
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=x.device)
+    _check("tt_round_backward",
+           lib.tt_round_backward(a.ref(), float(eps), int(max_rank), b.ref(), c.ref(),
+                                 ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(need), _stream_ptr(stream)))
+    return gx
+
+
 def tt_eval_backward(x: TT, digits: torch.Tensor, dvalues: torch.Tensor, stream=None) -> TT:
     lib = load()
     n = int(digits.shape[0])

@@ -99,3 +99,56 @@ def test_eval_full_size_sampled(cuda_lib):
     ref = core.evaluate([c.astype(np.float64) for c in x], dg[idx])
     rms = np.sqrt(np.mean(ref ** 2))
     assert np.max(np.abs(got[idx] - ref)) <= 1e-5 * rms * 4
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-10), (torch.float32, 1e-4)])
+def test_residual_gradient_full_size(cuda_lib, dtype, tol):
+    """||A x - b||^2 at the fitting workload's size: L = 40 (2 x 20 bits), rank 64, the 2D
+    Laplacian (rank 5, so A x has rank 320), b of rank 16; gradient w.r.t. the cores of x."""
+    bits = 20
+    L = 2 * bits
+    w = qtt.laplacian_mpo(2, bits)
+    x = inputs.random_tt(240, L, 2, 64)
+    b = inputs.random_tt(241, L, 2, 16)
+    if dtype == torch.float32:
+        x = [c.astype(np.float32).astype(np.float64) for c in x]
+        b = [c.astype(np.float32).astype(np.float64) for c in b]
+        w = [c.astype(np.float32).astype(np.float64) for c in w]
+    ws = [torch.tensor(c, dtype=dtype, device="cuda") for c in w]
+    xs = _params(x, dtype)
+    bs = [torch.tensor(c, dtype=dtype, device="cuda") for c in b]
+    y = tt_apply_ad(ws, xs)
+    r2 = tt_inner_ad(y, y) - 2 * tt_inner_ad(y, bs) + tt_inner_ad(bs, bs)
+    r2.backward()
+    ref = grad.residual_loss_grad(w, x, b)
+    assert _close([p.grad for p in xs], ref, tol)
+
+
+def test_fit_gradient_full_size(cuda_lib):
+    """The fit gradient at 2^20 samples, L = 40, rank 64, FP32: the oracle's gradient on the
+    first 8192 samples against the GPU's on the same samples, and the full-batch GPU gradient
+    against the sum of its gradients over 128 sample blocks (the gradient is linear in the
+    per-sample weights, so the blocks must add up to the whole)."""
+    tt = cuda_lib
+    bits, n, blk = 20, 1 << 20, 8192
+    L = 2 * bits
+    x = [c.astype(np.float32) for c in inputs.random_tt(250, L, 2, 64)]
+    x64 = [c.astype(np.float64) for c in x]
+    dg = inputs.random_digits(251, n, [2] * L)
+    f = inputs.fit_targets(dg, bits)
+    X = tt.TT.from_numpy(x, dtype=torch.float32)
+    d = torch.as_tensor(dg, device="cuda")
+    v = tt.tt_eval(X, d)
+    w = (v.double() - torch.as_tensor(f, device="cuda")) / n
+    g_full = tt.tt_eval_backward(X, d, w.float())
+    # parity with the oracle on one block
+    g0 = tt.tt_eval_backward(X, d[:blk], w[:blk].float())
+    ref0 = grad.evaluate_vjp(x64, dg[:blk], w[:blk].cpu().numpy())
+    assert _close(g0.cores, ref0, 1e-4)
+    # linearity in the samples over the whole batch
+    acc = [np.zeros(c.shape) for c in x]
+    for s0 in range(0, n, blk):
+        gb = tt.tt_eval_backward(X, d[s0:s0 + blk], w[s0:s0 + blk].float())
+        for a, c in zip(acc, gb.cores):
+            a += c.double().cpu().numpy()
+    assert _close(g_full.cores, acc, 1e-5)
