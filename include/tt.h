@@ -274,10 +274,12 @@ void tt_profile_enable(int32_t on);
 int tt_profile_read(int32_t cls, double* ms, double* nominal_flops, uint64_t* count);
 
 /* Executed work of a profiler class since tt_profile_enable(1), where it differs from the
- * nominal count: for class 0 the Jacobi sweeps that actually ran, 6 p^3 flops per sweep of a
- * p x p factor (every pair of columns: three dot products and one rotation of length p);
- * bonds whose SVD the full-rank certificate skipped contribute nothing.  The other classes
- * equal their nominal flops.  TT_ERR_ARG for an unknown class. */
+ * nominal count: for class 0 the Jacobi work that actually ran - per sweep of a p x p factor
+ * the three dot products of every pair of columns (6 p flops a pair), plus 6 p flops for each
+ * rotation applied (FP64 form; the mixed form's FP32 sweeps count 12 p flops a pair), plus the
+ * QR of R^T that preconditions FP64 factors (4 p^3 / 3); bonds whose SVD the full-rank
+ * certificate skipped contribute nothing.  The other classes equal their nominal flops.
+ * TT_ERR_ARG for an unknown class. */
 int tt_profile_read_executed(int32_t cls, double* executed_flops);
 
 /* C = alpha A B + beta C in FP32 on the tensor cores: TF32 with a 3-term hi/lo split

@@ -324,12 +324,25 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         TT_TRY(read_back(s, B.sv.rank, &rk[0], sizeof(int)));
         TT_TRY(read_back(s, B.sv.sweeps, &rk[1], sizeof(int)));
         total_sweeps += rk[1];
-        // executed work of the Jacobi: every sweep visits the p (p - 1) / 2 pairs, each with
-        // three dot products and a rotation of two length-p columns (12 p flops): <= 6 p^3
-        // per sweep (FP32 sweeps of the mixed form and its FP64 finish counted alike)
-        {
-          const int sw = mixed_svd ? (sweeps32 < 0 ? 30 + std::max(rk[1], 0) : sweeps32) : rk[1];
-          prof.set_executed(pe_jacobi, 6.0 * (double)p * p * p * std::max(sw, 0) + precond_flops);
+        // executed work of the Jacobi: every sweep forms the three dot products of each of
+        // the p (p - 1) / 2 pairs (6 p flops), and each rotation that was applied costs 6 p
+        // more (the kernels count them per sweep); the mixed form's FP32 sweeps are bounded
+        // by 12 p flops per pair
+        if (prof.on) {
+          double ex = precond_flops;
+          const double pairs = 0.5 * (double)p * (p - 1);
+          if (mixed_svd) {
+            const int sw = sweeps32 < 0 ? 30 + std::max(rk[1], 0) : sweeps32;
+            ex += 12.0 * p * pairs * std::max(sw, 0);
+          } else {
+            const int sw = std::max(0, std::min(rk[1], (int)SvdWork::kMaxSweeps));
+            std::vector<unsigned> rots(std::max(sw, 1), 0u);
+            if (sw > 0) TT_TRY(read_back(s, B.sv.rot, rots.data(), sw * sizeof(unsigned)));
+            double nrot = 0.0;
+            for (int q = 0; q < sw; ++q) nrot += rots[q];
+            ex += 6.0 * p * (pairs * sw + nrot);
+          }
+          prof.set_executed(pe_jacobi, ex);
         }
         prof.flush();
         tm.mark(6);
