@@ -447,7 +447,10 @@ def bench_eval(tt, dev, n=1 << 20, L=40, r=64):
             "samples_per_s": round(n / (ms * 1e-3), 1), "value": round(fl / (ms * 1e-3) / 1e9, 2),
             "unit": "GFLOP/s",
             "backward": {"ms": round(ms_b, 3), "samples_per_s": round(n / (ms_b * 1e-3), 1),
-                         "what": "tt_eval_backward (gradient w.r.t. the cores), FP64 prefixes/suffixes"}}
+                         "value": round(3 * fl / (ms_b * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+                         "flops": "3x the forward: prefix sweep, suffix sweep, per-site sums",
+                         "what": "tt_eval_backward (gradient w.r.t. the cores): FP32 prefix/suffix states "
+                                 "and per-site sums over 2048-sample slices, FP64 across slices"}}
 
 
 def bench_small(tt, dev, reps=50):
@@ -461,6 +464,8 @@ def bench_small(tt, dev, reps=50):
     W = tt.MPO.from_numpy(qtt.second_difference_mpo(10), device=dev)
     ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
     ts = []
+    lib = tt.load()
+    n0 = lib.tt_launch_count()
     for i in range(reps + 5):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -469,10 +474,11 @@ def bench_small(tt, dev, reps=50):
         torch.cuda.synchronize(dev)
         if i >= 5:
             ts.append((time.perf_counter() - t0) * 1e6)
+    launches = (lib.tt_launch_count() - n0) / (reps + 5)
     return {"workload": "1D quantics TT L=10, rank 8, second-difference MPO rank 3, apply + tt_round "
                         "eps=1e-10, FP64 (host-timed, median of 50)",
             "us_per_step": round(float(np.median(ts)), 1), "us_min": round(float(np.min(ts)), 1),
-            "ranks_out": Z.ranks}
+            "launches_per_step": launches, "ranks_out": Z.ranks}
 
 
 def cpu_baseline(x_np, W_np, eps, flops_step, repeats=2):

@@ -235,14 +235,18 @@ int tt_hadamard_backward(const tt_train* x, const tt_train* y, const tt_train* d
 int tt_inner_backward(const tt_train* x, const tt_train* y, double dout, tt_train* dx,
                       tt_train* dy, void* workspace, size_t ws_bytes, void* stream);
 
-/* Device workspace (bytes) that tt_eval_backward needs for n samples.  Samples
- * are processed in chunks of at most 16384, so the size stops growing beyond that. */
+/* Device workspace (bytes) that tt_eval_backward needs for n samples.  Samples are
+ * processed in chunks whose prefix and suffix states take at most 1 GiB (at most 65536
+ * samples), so the size stops growing beyond one chunk. */
 size_t tt_eval_backward_workspace_size(const tt_train* x, int64_t n);
 
 /* dG_k[:, i, :] += sum_{s : i_k^s = i} dvalues_s prefix_s^T suffix_s, where
  * prefix_s = G_1[:, i_1^s, :] ... G_{k-1}[:, i_{k-1}^s, :] and suffix_s is the
- * product of the cores right of k.  Prefixes and suffixes and the per-site
- * reduction over samples are FP64.  dvalues: device [n], x's dtype.  Asynchronous. */
+ * product of the cores right of k (paper Sec. 3.4, evaluation; the gradient is linear in
+ * dvalues).  Prefixes and suffixes are formed and stored in x's dtype; the sums over
+ * samples run in x's dtype over slices of at most 2048 samples and are accumulated across
+ * slices in FP64.  Samples whose digit at a site is out of range add nothing there.
+ * dvalues: device [n], x's dtype.  Cores of dx that are NULL are skipped.  Asynchronous. */
 int tt_eval_backward(const tt_train* x, const uint8_t* digits, int64_t n, const void* dvalues,
                      tt_train* dx, void* workspace, size_t ws_bytes, void* stream);
 

@@ -13,6 +13,11 @@ each repetition and the output ranks.  `--op hadamard` rounds x (.) x instead.
 runs tt_apply_round_batched on the uneven batch instead: trains with L ~ U[20, 60],
 ranks ~ U[8, 128], each with its own random MPO of rank 3..5 (seed 4).
 
+    python -m paper_2602_20226_gb300.cli --eval 65536 --n-dims 2 --bits 20 --rank 64
+
+times tt_eval and tt_eval_backward of the FP32 train (seed 230) at that many uniform index
+tuples (seed 231), with CUDA events.
+
     python -m paper_2602_20226_gb300.cli --gemm 4096 --gemm-form sliced --repeat 10
 
 times one FP32 tensor-core GEMM (N x N x N, N(0, 1) operands, seed 1) with CUDA events
@@ -41,11 +46,14 @@ def main(argv=None) -> None:
     ap.add_argument("--batch", type=int, default=0, help="trains of the uneven batch (0: one train)")
     ap.add_argument("--gemm", type=int, default=0, help="size N of one N x N x N FP32 GEMM to time (0: none)")
     ap.add_argument("--gemm-form", choices=["sliced", "tf32x3"], default="sliced")
+    ap.add_argument("--eval", type=int, default=0, help="samples of tt_eval / tt_eval_backward to time (0: none)")
     a = ap.parse_args(argv)
     if a.batch > 0:
         return _batch(a)
     if a.gemm > 0:
         return _gemm(a)
+    if a.eval > 0:
+        return _eval(a)
 
     dtype = torch.float64 if a.form == "fp64" else torch.float32
     prec = _abi.TT_PREC_FP64 if a.form == "fp64" else _abi.TT_PREC_MIXED
@@ -83,6 +91,25 @@ def _batch(a) -> None:
         torch.cuda.synchronize()
         print(f"[{i}] {a.form} batch of {a.batch}: {(time.perf_counter() - t) * 1e3:.1f} ms, "
               f"max rank {max(max(o.ranks) for o in outs)}", flush=True)
+
+
+def _eval(a) -> None:
+    import numpy as np
+
+    L, n = a.n_dims * a.bits, a.eval
+    X = api.TT.from_numpy([c.astype(np.float32) for c in inputs.random_tt(230, L, 2, a.rank)], dtype=torch.float32)
+    dg = torch.as_tensor(inputs.random_digits(231, n, [2] * L), device="cuda")
+    dv = torch.as_tensor(np.random.default_rng(232).standard_normal(n).astype(np.float32), device="cuda")
+    for i in range(a.repeat):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        api.tt_eval(X, dg)
+        e[1].record()
+        api.tt_eval_backward(X, dg, dv)
+        e[2].record()
+        e[2].synchronize()
+        print(f"[{i}] eval of {n} samples, L={L}, rank {a.rank}: forward {e[0].elapsed_time(e[1]):.3f} ms, "
+              f"backward {e[1].elapsed_time(e[2]):.3f} ms", flush=True)
 
 
 def _gemm(a) -> None:

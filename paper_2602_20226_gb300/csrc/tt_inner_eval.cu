@@ -147,6 +147,247 @@ __global__ void eval_staged_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
   if (active) values[smp] = cur[tid];
 }
 
+// ------------------------------------------------------------------ eval backward
+// The adjoint of evaluation is, per site k and digit i, a contraction over samples:
+//   dG_k[:, i, :] = sum_{s : i_k^s = i} w_s p_{k,s}^T q_{k,s}
+// with p_{k,s} = G_1[:, i_1^s, :] ... G_{k-1}[:, i_{k-1}^s, :] (the row vector in front of
+// site k) and q_{k,s} = G_{k+1}[:, i_{k+1}^s, :] ... G_L[:, i_L^s, :] (the column vector after
+// it).  For a chunk of C samples, eval_states_kernel stores every p_k and q_k (state-major,
+// [j][C], so that a thread per sample writes coalesced rows), one CTA of samples sweeping
+// left to right and one right to left in the same launch; eval_bwd_accum_kernel then forms
+// the per-site sums as (r_{k-1} x samples) . (samples x r_k) products, the samples of each
+// digit taken from a per-tile list, and adds them into FP64 accumulators.
+
+// Offsets (elements) of the prefix and suffix states of site k inside a chunk's store.
+__device__ __forceinline__ long long prefix_off(const int* r, int k, long long C) {
+  long long o = 0;
+  for (int j = 0; j < k; ++j) o += r[j];
+  return o * C;
+}
+__device__ __forceinline__ long long suffix_off(const int* r, int L, int k, long long C) {
+  long long o = 0;
+  for (int j = 0; j < L; ++j) o += r[j];  // the prefix block comes first
+  for (int j = 0; j < k; ++j) o += r[j + 1];
+  return o * C;
+}
+
+// blockIdx.y = 0: prefixes (left to right), 1: suffixes (right to left).  Same staging and
+// inner loop as eval_staged_kernel; for the suffixes the core is staged transposed
+// (row (b, i) holds G[:, i, b]), so that both directions form out = cur . stage-rows.
+template <typename T, int JB>
+__global__ void eval_states_kernel(EvalParams<T> P, const uint8_t* __restrict__ digits, long long n,
+                                   T* __restrict__ states, long long C, int stage_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = blockDim.x;
+  const int tid = threadIdx.x;
+  const bool suffix = blockIdx.y == 1;
+  T* cur = reinterpret_cast<T*>(smem_raw);
+  T* nxt = cur + (size_t)P.rmax * S;
+  T* stage = nxt + (size_t)P.rmax * S;
+  uint8_t* dg = reinterpret_cast<uint8_t*>(stage + stage_elems + JB);
+  const long long s0 = (long long)blockIdx.x * S;
+  const long long smp = s0 + tid;
+  const bool active = smp < n;
+  {
+    const long long nb = (long long)min((long long)S, n - s0) * P.L;
+    const uint8_t* src = digits + s0 * P.L;
+    for (long long e = tid; e < nb; e += S) dg[e] = src[e];
+  }
+  cur[tid] = T(1);
+  constexpr int VW = 16 / sizeof(T);
+  using V = std::conditional_t<sizeof(T) == 4, float4, double2>;
+  const int L = P.L;
+  for (int step = 0; step < L; ++step) {
+    const int k = suffix ? L - 1 - step : step;
+    const int r0 = P.r[k], r1 = P.r[k + 1], d = P.d[k];
+    const int rin = suffix ? r1 : r0, rout = suffix ? r0 : r1;
+    // the state in front of site k (prefix) or after it (suffix)
+    if (active) {
+      T* dst = states + (suffix ? suffix_off(P.r, L, k, C) : prefix_off(P.r, k, C)) + smp;
+      for (int j = 0; j < rin; ++j) dst[(long long)j * C] = cur[(size_t)j * S + tid];
+    }
+    if (step == L - 1) break;  // the full product is not needed
+    const int routp = eval_row_pad<T>(rout);
+    __syncthreads();
+    {
+      const T* G = P.g[k];
+      const int total = r0 * d * r1;
+      for (int e = tid; e < total; e += S) {
+        const int row = e / r1, c = e - row * r1;  // row = a d + i, c = b
+        if (!suffix) {
+          stage[row * routp + c] = G[e];
+        } else {
+          const int a = row / d, i = row - a * d;
+          stage[(c * d + i) * routp + a] = G[e];
+        }
+      }
+    }
+    __syncthreads();
+    int dig = active ? (int)dg[tid * L + k] : 0;
+    if (dig >= d) dig = 0;  // the accumulation skips such samples at this site
+    for (int j0 = 0; j0 < rout; j0 += JB) {
+      T acc[JB];
+#pragma unroll
+      for (int t = 0; t < JB; ++t) acc[t] = T(0);
+      for (int a = 0; a < rin; ++a) {
+        const T v = cur[(size_t)a * S + tid];
+        const V* g = reinterpret_cast<const V*>(stage + (size_t)(a * d + dig) * routp + j0);
+#pragma unroll
+        for (int q = 0; q < JB / VW; ++q) {
+          const V w = g[q];
+          if constexpr (VW == 4) {
+            acc[4 * q + 0] = fma(v, w.x, acc[4 * q + 0]);
+            acc[4 * q + 1] = fma(v, w.y, acc[4 * q + 1]);
+            acc[4 * q + 2] = fma(v, w.z, acc[4 * q + 2]);
+            acc[4 * q + 3] = fma(v, w.w, acc[4 * q + 3]);
+          } else {
+            acc[2 * q + 0] = fma(v, w.x, acc[2 * q + 0]);
+            acc[2 * q + 1] = fma(v, w.y, acc[2 * q + 1]);
+          }
+        }
+      }
+      const int jn = min(JB, rout - j0);
+#pragma unroll
+      for (int t = 0; t < JB; ++t)
+        if (t < jn) nxt[(size_t)(j0 + t) * S + tid] = acc[t];
+    }
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+}
+
+// Per-site accumulation over one slice of a chunk's samples.  Grid: x = sample slice,
+// y = (a, b) tile of 64 x 64, z = site * digit groups + group.  128 threads, each owning an
+// 8 x 4 block of the tile for DG digits (registers); samples go through shared memory in
+// tiles of 32 (prefix scaled by w_s, both transposed to sample-major rows), and for each
+// digit of the group the CTA walks only the samples that carry it (a list built by ballot),
+// so the work is r_{k-1} r_k multiply-adds per sample and site.  The slice's sums (in T)
+// are added into the FP64 accumulator acc[k] with one atomic per entry.
+constexpr int kAccTile = 64, kAccK = 32;
+
+struct SiteMask {
+  unsigned char on[TT_MAX_SITES];
+};
+
+template <typename T, int DG>
+__global__ void __launch_bounds__(128) eval_bwd_accum_kernel(EvalParams<T> P, SiteMask want,
+                                                            const uint8_t* __restrict__ digits, const T* __restrict__ w,
+                                                            long long n, const T* __restrict__ states, long long C,
+                                                            long long slice, double* __restrict__ acc) {
+  constexpr int PS = kAccTile + 4;  // row stride of the staged tiles (16-byte rows, fewer conflicts)
+  __shared__ __align__(16) T Ps[kAccK][PS];
+  __shared__ __align__(16) T Qs[kAccK][PS];
+  __shared__ int list[DG][kAccK];
+  __shared__ int cnt[DG];
+  const int L = P.L;
+  const int tid = threadIdx.x;
+  int kz = blockIdx.z;
+  int k = 0;
+  // site and digit group of this CTA
+  {
+    int z = kz;
+    for (k = 0; k < L; ++k) {
+      const int g = (P.d[k] + DG - 1) / DG;
+      if (z < g) break;
+      z -= g;
+    }
+    kz = z;  // digit group within site k
+  }
+  if (k >= L || !want.on[k]) return;
+  const int r0 = P.r[k], r1 = P.r[k + 1], d = P.d[k];
+  const int ntb = (r1 + kAccTile - 1) / kAccTile;
+  const int a0 = (blockIdx.y / ntb) * kAccTile, b0 = (blockIdx.y % ntb) * kAccTile;
+  if (a0 >= r0) return;
+  const int i0 = kz * DG;
+  const T* Pk = states + prefix_off(P.r, k, C);
+  const T* Qk = states + suffix_off(P.r, L, k, C);
+  const long long sb = (long long)blockIdx.x * slice, se = min(n, sb + slice);
+  const int ta = tid >> 4, tb = tid & 15;  // 8 x 16 threads: rows ta*8.., columns tb*4..
+  T accr[DG][8][4];
+#pragma unroll
+  for (int g = 0; g < DG; ++g)
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) accr[g][x][y] = T(0);
+  for (long long t0 = sb; t0 < se; t0 += kAccK) {
+    const int kt = (int)min((long long)kAccK, se - t0);
+    __syncthreads();  // the previous tile is consumed
+    // stage p (times w) and q: element e -> (row j, sample s), coalesced along samples
+    for (int e = tid; e < kAccTile * kAccK; e += 128) {
+      const int j = e / kAccK, s = e - j * kAccK;
+      T pv = T(0), qv = T(0);
+      if (s < kt) {
+        if (a0 + j < r0) pv = Pk[(long long)(a0 + j) * C + t0 + s] * w[t0 + s];
+        if (b0 + j < r1) qv = Qk[(long long)(b0 + j) * C + t0 + s];
+      }
+      Ps[s][j] = pv;
+      Qs[s][j] = qv;
+    }
+    if (tid < 32) {
+      const int dgt = tid < kt ? (int)digits[(t0 + tid) * L + k] : -1;
+#pragma unroll
+      for (int g = 0; g < DG; ++g) {
+        const unsigned m = __ballot_sync(0xffffffffu, dgt == i0 + g && i0 + g < d);
+        if (dgt == i0 + g && i0 + g < d) list[g][__popc(m & ((1u << tid) - 1u))] = tid;
+        if (tid == 0) cnt[g] = __popc(m);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < DG; ++g) {
+      const int c = cnt[g];
+      for (int q = 0; q < c; ++q) {
+        const int s = list[g][q];
+        T pa[8], qb[4];
+        if constexpr (sizeof(T) == 4) {
+          const float4 u0 = *reinterpret_cast<const float4*>(&Ps[s][ta * 8]);
+          const float4 u1 = *reinterpret_cast<const float4*>(&Ps[s][ta * 8 + 4]);
+          const float4 v0 = *reinterpret_cast<const float4*>(&Qs[s][tb * 4]);
+          pa[0] = u0.x; pa[1] = u0.y; pa[2] = u0.z; pa[3] = u0.w;
+          pa[4] = u1.x; pa[5] = u1.y; pa[6] = u1.z; pa[7] = u1.w;
+          qb[0] = v0.x; qb[1] = v0.y; qb[2] = v0.z; qb[3] = v0.w;
+        } else {
+#pragma unroll
+          for (int x = 0; x < 8; x += 2) {
+            const double2 u = *reinterpret_cast<const double2*>(&Ps[s][ta * 8 + x]);
+            pa[x] = u.x;
+            pa[x + 1] = u.y;
+          }
+#pragma unroll
+          for (int y = 0; y < 4; y += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(&Qs[s][tb * 4 + y]);
+            qb[y] = v.x;
+            qb[y + 1] = v.y;
+          }
+        }
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) accr[g][x][y] = fma(pa[x], qb[y], accr[g][x][y]);
+      }
+    }
+  }
+  double* acck = acc;
+  for (int j = 0; j < k; ++j) acck += (size_t)P.r[j] * P.d[j] * P.r[j + 1];
+#pragma unroll
+  for (int g = 0; g < DG; ++g) {
+    const int i = i0 + g;
+    if (i >= d) continue;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int a = a0 + ta * 8 + x;
+      if (a >= r0) continue;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int b = b0 + tb * 4 + y;
+        if (b < r1 && accr[g][x][y] != T(0)) atomicAdd(acck + ((size_t)a * d + i) * r1 + b, (double)accr[g][x][y]);
+      }
+    }
+  }
+}
+
 // Backward of evaluation for one site k: dG_k[a, i, b] += sum_s w_s P_s[a] Sf_s[b] [i_k^s == i].
 // prefixes P (n x r0) and suffixes Sf (n x r1) are given row-major in FP64.
 template <typename T>
@@ -403,10 +644,11 @@ int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values,
   return TT_OK;
 }
 
-// Samples are processed in chunks so that the prefix store stays bounded.
+// Fallback for trains whose cores do not fit the staged kernels: samples in chunks of 16384,
+// FP64 prefixes and suffixes, one thread per output element and per (a, b) of a site.
 constexpr int64_t kEvalBwdChunk = 16384;
 
-size_t eval_backward_workspace_bytes(const tt_train* x, int64_t n) {
+size_t eval_backward_generic_bytes(const tt_train* x, int64_t n) {
   const int64_t c = std::max<int64_t>(1, std::min<int64_t>(n, kEvalBwdChunk));
   int64_t rmax = 1, gmax = 1, pre = 0;
   for (int k = 0; k <= x->L; ++k) {
@@ -418,11 +660,8 @@ size_t eval_backward_workspace_bytes(const tt_train* x, int64_t n) {
 }
 
 template <typename T>
-int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, const void* dvalues,
-                       tt_train* dx, void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (n == 0) return TT_OK;
-  if (ws_bytes < eval_backward_workspace_bytes(x, n))
-    return fail(TT_ERR_WORKSPACE, "tt_eval_backward: workspace too small");
+int eval_backward_generic(const tt_train* x, const uint8_t* digits, int64_t n, const void* dvalues,
+                          tt_train* dx, void* ws, cudaStream_t s) {
   const int L = x->L;
   const int64_t chunk = std::min<int64_t>(n, kEvalBwdChunk);
   int64_t rmax = 1;
@@ -473,6 +712,138 @@ int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, cons
         std::swap(sA, sB);
       }
     }
+  }
+  return TT_OK;
+}
+
+// Staged path: shared memory of eval_states_kernel (two row buffers of S samples, the largest
+// staged core in either orientation, the CTA's digits).
+constexpr int kStatesS = 128, kStatesJB = 16;
+constexpr size_t kStatesSmemMax = 110 * 1024;
+constexpr size_t kStateBudget = size_t(1) << 30;  // bytes of prefix + suffix states per chunk
+
+template <typename T>
+int states_stage_elems(const tt_train* x) {
+  int stage = 1;
+  for (int k = 0; k < x->L; ++k) {
+    const int r0 = (int)x->ranks[k], r1 = (int)x->ranks[k + 1], d = x->d[k];
+    stage = std::max(stage, std::max(r0 * d * eval_row_pad<T>(r1), r1 * d * eval_row_pad<T>(r0)));
+  }
+  return stage;
+}
+
+template <typename T>
+size_t states_smem(const tt_train* x) {
+  int rmax = 1;
+  for (int k = 0; k <= x->L; ++k) rmax = std::max<int>(rmax, (int)x->ranks[k]);
+  return (2 * (size_t)rmax * kStatesS + states_stage_elems<T>(x) + kStatesJB) * sizeof(T) +
+         (size_t)kStatesS * x->L + 16;
+}
+
+// samples per chunk of the state store, and the store's elements per sample
+template <typename T>
+int64_t states_chunk(const tt_train* x, int64_t n, int64_t* per_sample) {
+  int64_t per = 0;
+  for (int k = 0; k < x->L; ++k) per += x->ranks[k] + x->ranks[k + 1];
+  if (per_sample) *per_sample = per;
+  int64_t c = (int64_t)(kStateBudget / ((size_t)per * sizeof(T))) & ~int64_t(127);
+  c = std::max<int64_t>(128, std::min<int64_t>(c, 65536));
+  return std::max<int64_t>(1, std::min<int64_t>(c, n));
+}
+
+template <typename T>
+size_t eval_backward_staged_bytes(const tt_train* x, int64_t n) {
+  int64_t per = 0;
+  const int64_t C = states_chunk<T>(x, n, &per);
+  int64_t g = 0;
+  for (int k = 0; k < x->L; ++k) g += x->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1];
+  return ((size_t)C * per * sizeof(T) + 255) / 256 * 256 + (size_t)g * sizeof(double) + 1024;
+}
+
+template <typename T>
+bool eval_backward_staged_fits(const tt_train* x) {
+  return states_smem<T>(x) <= kStatesSmemMax;
+}
+
+size_t eval_backward_workspace_bytes(const tt_train* x, int64_t n) {
+  if (x->dtype == TT_F64)
+    return eval_backward_staged_fits<double>(x) ? eval_backward_staged_bytes<double>(x, n)
+                                                : eval_backward_generic_bytes(x, n);
+  return eval_backward_staged_fits<float>(x) ? eval_backward_staged_bytes<float>(x, n)
+                                             : eval_backward_generic_bytes(x, n);
+}
+
+template <typename T>
+int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, const void* dvalues,
+                       tt_train* dx, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (n == 0) return TT_OK;
+  if (ws_bytes < eval_backward_workspace_bytes(x, n))
+    return fail(TT_ERR_WORKSPACE, "tt_eval_backward: workspace too small");
+  if (!eval_backward_staged_fits<T>(x)) return eval_backward_generic<T>(x, digits, n, dvalues, dx, ws, s);
+  const int L = x->L;
+  EvalParams<T> P;
+  P.L = L;
+  P.rmax = 1;
+  SiteMask want;
+  bool any = false;
+  for (int k = 0; k < L; ++k) {
+    P.g[k] = static_cast<const T*>(x->cores[k]);
+    P.d[k] = x->d[k];
+    P.r[k] = (int)x->ranks[k];
+    P.rmax = std::max<int>(P.rmax, (int)x->ranks[k]);
+    want.on[k] = dx->cores[k] != nullptr;
+    any = any || want.on[k];
+  }
+  P.r[L] = (int)x->ranks[L];
+  if (!any) return TT_OK;
+  int64_t per = 0;
+  const int64_t C = states_chunk<T>(x, n, &per);
+  T* states = static_cast<T*>(ws);
+  double* acc = reinterpret_cast<double*>(static_cast<char*>(ws) + ((size_t)C * per * sizeof(T) + 255) / 256 * 256);
+  int64_t g = 0, zdim = 0;
+  constexpr int DG = sizeof(T) == 4 ? 2 : 1;
+  int tiles = 1;
+  for (int k = 0; k < L; ++k) {
+    g += x->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1];
+    zdim += (x->d[k] + DG - 1) / DG;
+    tiles = std::max<int>(tiles, (int)(ceil_div(x->ranks[k], kAccTile) * ceil_div(x->ranks[k + 1], kAccTile)));
+  }
+  if (zdim > 65535 || tiles > 65535) return fail(TT_ERR_UNSUPPORTED, "tt_eval_backward: train too large");
+  TT_CUDA_CHECK(cudaMemsetAsync(acc, 0, (size_t)g * sizeof(double), s));
+  const size_t smem = states_smem<T>(x);
+  const int stage = states_stage_elems<T>(x);
+  static int configured[2] = {-1, -1};
+  int dev = 0;
+  TT_CUDA_CHECK(cudaGetDevice(&dev));
+  const int which = sizeof(T) == 8 ? 0 : 1;
+  if (configured[which] != dev) {
+    TT_CUDA_CHECK(cudaFuncSetAttribute(eval_states_kernel<T, kStatesJB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kStatesSmemMax));
+    configured[which] = dev;
+  }
+  // slices of at most 2048 samples (the FP32 sums of a slice stay short) and enough CTAs to fill the GPU
+  const int64_t slice_target = std::max<int64_t>(256, std::min<int64_t>(2048, C / std::max<int64_t>(1, ceil_div(4 * num_sms(), zdim * tiles))));
+  for (int64_t c0 = 0; c0 < n; c0 += C) {
+    const int64_t cn = std::min<int64_t>(C, n - c0);
+    const uint8_t* dg = digits + c0 * L;
+    const T* w = static_cast<const T*>(dvalues) + c0;
+    eval_states_kernel<T, kStatesJB><<<dim3((unsigned)ceil_div(cn, kStatesS), 2), kStatesS, smem, s>>>(
+        P, dg, cn, states, C, stage);
+    TT_LAUNCH_CHECK();
+    const int64_t slice = (std::min<int64_t>(slice_target, cn) + kAccK - 1) / kAccK * kAccK;
+    const dim3 grid((unsigned)ceil_div(cn, slice), (unsigned)tiles, (unsigned)zdim);
+    eval_bwd_accum_kernel<T, DG><<<grid, 128, 0, s>>>(P, want, dg, w, cn, states, C, slice, acc);
+    TT_LAUNCH_CHECK();
+  }
+  const int TPB = 256;
+  int64_t off = 0;
+  for (int k = 0; k < L; ++k) {
+    const int64_t gk = x->ranks[k] * (int64_t)x->d[k] * x->ranks[k + 1];
+    if (want.on[k]) {
+      add_into_kernel<T><<<(unsigned)ceil_div(gk, TPB), TPB, 0, s>>>(acc + off, gk, static_cast<T*>(dx->cores[k]));
+      TT_LAUNCH_CHECK();
+    }
+    off += gk;
   }
   return TT_OK;
 }

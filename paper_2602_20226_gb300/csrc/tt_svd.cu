@@ -32,6 +32,25 @@ __device__ __forceinline__ bool sweep_barrier(unsigned* bar, unsigned* status) {
   return grid_barrier(bar, gridDim.x, status);
 }
 
+// Sum of (a, b, c) over a warp with 6 FP64 additions per lane instead of 15: the first two
+// butterfly levels halve the number of values each lane carries ((a, b, c, 0) -> two -> one),
+// the last three sum the one left.  On return the lane holds the total of value
+// (lane >> 3) & 3 of (a, b, c, 0): lanes 0-7 a, 8-15 b, 16-23 c.
+__device__ __forceinline__ double warp_sum3_split(double a, double b, double c, int lane) {
+  const bool hi16 = lane & 16;
+  double k0 = hi16 ? c : a, k1 = hi16 ? 0.0 : b;
+  const double s0 = hi16 ? a : c, s1 = hi16 ? b : 0.0;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool hi8 = lane & 8;
+  double k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
 // Columns of up to 32 * TPL rows are held in registers for the whole pair update
 // (all loads issued at once, one store pass); TPL = 0 streams longer columns.
 template <int TPL>
@@ -40,17 +59,26 @@ __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __r
   double al = 0.0, be = 0.0, ga = 0.0;
   double ra[TPL > 0 ? TPL : 1], rb[TPL > 0 ? TPL : 1];
   if (TPL > 0) {
+    // chunks wholly beyond nrow are skipped by a warp-uniform test (an FP64 instruction with
+    // every lane predicated off still takes its 16 clocks of the SM's FP64 pipe)
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
-      const int i = lane + 32 * t;
-      ra[t] = (i < nrow) ? __ldcg(xa + i) : 0.0;
-      rb[t] = (i < nrow) ? __ldcg(xb + i) : 0.0;
+      ra[t] = rb[t] = 0.0;
+      if (32 * t < nrow) {
+        const int i = lane + 32 * t;
+        if (i < nrow) {
+          ra[t] = __ldcg(xa + i);
+          rb[t] = __ldcg(xb + i);
+        }
+      }
     }
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
-      al = fma(ra[t], ra[t], al);
-      be = fma(rb[t], rb[t], be);
-      ga = fma(ra[t], rb[t], ga);
+      if (32 * t < nrow) {
+        al = fma(ra[t], ra[t], al);
+        be = fma(rb[t], rb[t], be);
+        ga = fma(ra[t], rb[t], ga);
+      }
     }
   } else {
     for (int i = lane; i < nrow; i += 32) {
@@ -60,9 +88,10 @@ __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __r
       ga = fma(u, v, ga);
     }
   }
-  al = warp_sum(al);
-  be = warp_sum(be);
-  ga = warp_sum(ga);
+  const double v = warp_sum3_split(al, be, ga, lane);
+  al = __shfl_sync(0xffffffffu, v, 0);
+  be = __shfl_sync(0xffffffffu, v, 8);
+  ga = __shfl_sync(0xffffffffu, v, 16);
   if (al < negl && be < negl) return false;  // both columns are truncated whatever the angle
   if (!(ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
   const double zeta = (be - al) / (2.0 * ga);
@@ -74,10 +103,12 @@ __device__ __forceinline__ bool rotate_pair(double* __restrict__ xa, double* __r
   if (TPL > 0) {
 #pragma unroll
     for (int q = 0; q < TPL; ++q) {
-      const int i = lane + 32 * q;
-      if (i < nrow) {
-        __stcg(xa + i, c * ra[q] - s * rb[q]);
-        __stcg(xb + i, s * ra[q] + c * rb[q]);
+      if (32 * q < nrow) {
+        const int i = lane + 32 * q;
+        if (i < nrow) {
+          __stcg(xa + i, c * ra[q] - s * rb[q]);
+          __stcg(xb + i, s * ra[q] + c * rb[q]);
+        }
       }
     }
   } else {
@@ -175,8 +206,13 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
 
 // The same FP64 Jacobi with one CTA of WPP warps per pair: the rows of the pair are split
 // over the warps (shorter dependent FMA chains, WPP times the warps per SM), the partial
-// sums are combined in shared memory in a fixed order, every warp derives the same
-// rotation and applies it to its rows.  Dataflow ordering between pairs as above.
+// sums are combined in shared memory in a fixed order, and one thread derives the rotation
+// for the whole CTA.  GB300's FP64 rate is 2 lanes per clock per SM, so every FP64
+// instruction a warp issues holds the SM's FP64 pipe for 16 clocks: the divisions and square
+// roots of the rotation (about 60 FP64 instructions) are issued once, not by every warp; the
+// warp sums take 6 additions per lane (warp_sum3_split); register chunks wholly beyond a
+// warp's rows are skipped by a warp-uniform test instead of being issued with every lane
+// predicated off.  Dataflow ordering between pairs as in jacobi_kernel.
 template <int WPP, int TPL>
 __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nrow, int ncol, int ldx, double tol,
                                                              double negl_scale, const double* norm, int max_sweeps,
@@ -189,7 +225,8 @@ __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nro
   const int rows = (nrow + WPP - 1) / WPP;  // rows of one warp
   const int i_lo = warp * rows, i_hi = min(nrow, i_lo + rows);
   __shared__ double red[WPP][3];
-  __shared__ int s_ok;
+  __shared__ double s_cs[2];
+  __shared__ int s_ok, s_doit;
   int sweep = 0;
   bool converged = false;
   unsigned t = 0;
@@ -225,55 +262,65 @@ __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nro
           double al = 0.0, be = 0.0, ga = 0.0;
 #pragma unroll
           for (int u = 0; u < TPL; ++u) {
-            const int i = i_lo + lane + 32 * u;
-            ra[u] = i < i_hi ? __ldcg(xa + i) : 0.0;
-            rb[u] = i < i_hi ? __ldcg(xb + i) : 0.0;
+            ra[u] = rb[u] = 0.0;
+            if (i_lo + 32 * u < i_hi) {  // warp-uniform
+              const int i = i_lo + lane + 32 * u;
+              if (i < i_hi) {
+                ra[u] = __ldcg(xa + i);
+                rb[u] = __ldcg(xb + i);
+              }
+            }
           }
 #pragma unroll
           for (int u = 0; u < TPL; ++u) {
-            al = fma(ra[u], ra[u], al);
-            be = fma(rb[u], rb[u], be);
-            ga = fma(ra[u], rb[u], ga);
+            if (i_lo + 32 * u < i_hi) {
+              al = fma(ra[u], ra[u], al);
+              be = fma(rb[u], rb[u], be);
+              ga = fma(ra[u], rb[u], ga);
+            }
           }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          ga = warp_sum(ga);
-          if (lane == 0) {
-            red[warp][0] = al;
-            red[warp][1] = be;
-            red[warp][2] = ga;
+          const double v = warp_sum3_split(al, be, ga, lane);
+          if ((lane & 7) == 0 && lane < 24) red[warp][lane >> 3] = v;
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            al = be = ga = 0.0;
+#pragma unroll
+            for (int w = 0; w < WPP; ++w) {
+              al += red[w][0];
+              be += red[w][1];
+              ga += red[w][2];
+            }
+            bool doit = !(al < negl && be < negl) && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be);
+            double c = 1.0, sn = 0.0;
+            if (doit) {
+              const double zeta = (be - al) / (2.0 * ga);
+              const double tn = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                                     : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+              c = 1.0 / sqrt(1.0 + tn * tn);
+              sn = c * tn;
+              doit = sn != 0.0;
+            }
+            s_cs[0] = c;
+            s_cs[1] = sn;
+            s_doit = doit;
+            if (doit) atomicAdd(rot + sweep, 1u);
           }
           __syncthreads();
-          al = be = ga = 0.0;
-#pragma unroll
-          for (int w = 0; w < WPP; ++w) {
-            al += red[w][0];
-            be += red[w][1];
-            ga += red[w][2];
-          }
-          bool doit = !(al < negl && be < negl) && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be);
-          double c = 1.0, sn = 0.0;
-          if (doit) {
-            const double zeta = (be - al) / (2.0 * ga);
-            const double tn = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                                   : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + tn * tn);
-            sn = c * tn;
-            doit = sn != 0.0;
-          }
-          if (doit) {
+          if (s_doit) {
+            const double c = s_cs[0], sn = s_cs[1];
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
-              const int i = i_lo + lane + 32 * u;
-              if (i < i_hi) {
-                __stcg(xa + i, c * ra[u] - sn * rb[u]);
-                __stcg(xb + i, sn * ra[u] + c * rb[u]);
+              if (i_lo + 32 * u < i_hi) {
+                const int i = i_lo + lane + 32 * u;
+                if (i < i_hi) {
+                  __stcg(xa + i, c * ra[u] - sn * rb[u]);
+                  __stcg(xb + i, sn * ra[u] + c * rb[u]);
+                }
               }
             }
-            if (threadIdx.x == 0) atomicAdd(rot + sweep, 1u);
           }
         }
-        __syncthreads();  // every warp's stores (and reads of red) precede the release
+        __syncthreads();  // every warp's stores (and reads of red / s_cs) precede the release
         if (threadIdx.x == 0) {
           __threadfence();
           st_release_u32(epoch + a, t + 1);

@@ -164,6 +164,31 @@ def test_inner_backward_parity(cuda_lib):
         assert _close(a, b, 1e-11, 1e-13)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_eval_backward_tiles_and_modes(cuda_lib, dtype):
+    """Ranks above one 64 x 64 accumulation tile (bond 80), mixed modes d in {2, 3, 5} (digit
+    groups of the accumulation), out-of-order digits and a ragged sample count.  FP32 cores
+    are rounded first, so both sides evaluate the same tensor; the FP32 bound allows FP32
+    states and slice sums (~1e-6 relative)."""
+    tt = cuda_lib
+    modes = [3, 2, 5, 2, 3, 2]
+    ranks = [1, 3, 6, 30, 80, 6, 2, 1][:len(modes) + 1]
+    ranks[-1] = 1
+    x = inputs.random_tt(120, len(modes), modes, ranks)
+    if dtype == torch.float32:
+        x = [c.astype(np.float32).astype(np.float64) for c in x]
+    n = 4099
+    dg = inputs.random_digits(121, n, modes)
+    w = inputs.rng(122).standard_normal(n)
+    g = tt.tt_eval_backward(tt.TT.from_numpy(x, dtype=dtype), torch.as_tensor(dg, device="cuda"),
+                            torch.as_tensor(w, device="cuda"))
+    ref = grad.evaluate_vjp(x, dg, w)
+    scale = max(np.abs(b).max() for b in ref)
+    tol = 1e-12 if dtype == torch.float64 else 2e-5
+    for a, b in zip(g.numpy(), ref):
+        assert np.abs(a.astype(np.float64) - b).max() <= tol * scale
+
+
 @pytest.mark.parametrize("n", [1, 300, 20000])
 def test_eval_backward_parity(cuda_lib, n):
     tt = cuda_lib
