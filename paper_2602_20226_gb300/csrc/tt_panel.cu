@@ -104,13 +104,18 @@ __device__ __forceinline__ void panel_fast_body(TIO* __restrict__ A, int lda, in
       const double* pt = P + t * ldp - lo;
       for (int l = r0 + g; l < hi; l += NRG) acc = fma(pc[l], pt[l], acc);
     }
-    red[g][t] = acc;
+    // a warp holds 32 / NB row groups of the same columns: fold them first (one shuffle
+    // level for NB = 16), then sum the warps' partials
+    static_assert(NB == 16 || NB == 32, "panel width");
+    if constexpr (NB == 16) acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    constexpr int NWP = NRG * NB / 32;  // warps
+    if (NB == 32 || (tid & 16) == 0) red[NB == 16 ? g >> 1 : g][t] = acc;
     if (own && g == 0) rowslot[b][t] = t < jb ? P[t * ldp + (c - lo)] : 0.0;
     __syncthreads();
     if (tid < NB) {
       double sum = 0.0;
 #pragma unroll
-      for (int q = 0; q < NRG; ++q) sum += red[q][tid];
+      for (int q = 0; q < NWP; ++q) sum += red[q][tid];
       slot[b][tid] = sum;
     }
     panel_sync<CS>();
@@ -131,8 +136,12 @@ __device__ __forceinline__ void panel_fast_body(TIO* __restrict__ A, int lda, in
       double tc = 0.0, sc = 1.0, beta = alpha;
       if (ss != 0.0) {
         beta = -copysign(sqrt(alpha * alpha + ss), alpha);
-        tc = (beta - alpha) / beta;
-        sc = 1.0 / (alpha - beta);
+        // tau = (beta - alpha) / beta and the scale 1 / (alpha - beta) from one division:
+        // with e = alpha - beta and q = 1 / (beta e), tau = -e^2 q, scale = beta q
+        const double e = alpha - beta;
+        const double q = 1.0 / (beta * e);
+        tc = -(e * e) * q;
+        sc = beta * q;
       }
       const double dd = rv + sc * S;
       if (lane < jb) sh_d[lane] = dd;

@@ -310,8 +310,11 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
             TT_TRY(extract_rt<T>(s, B.tmp, p, p, p, B.sv.X));
             precond_flops = 4.0 * (double)p * p * p / 3.0;
           }
-          // one-sided Jacobi on the columns of the square factor X (p x p)
-          TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30, delta_scale));
+          // one-sided Jacobi on the columns of the square factor X (p x p).  Pairs of columns
+          // that the truncation drops in any case are left alone, except when the adjoint
+          // records this run: it uses every singular pair (u_j, sigma_j) on its own, so the
+          // dropped ones must be converged as well
+          TT_TRY(jacobi_svd(s, B.sv, p, p, jacobi_tol<T>(p), 30, rec ? 0.0 : delta_scale));
         }
         const int pe_jacobi = pe;
         prof.end(pe, PROF_JACOBI, 12.0 * p * (double)p * p);

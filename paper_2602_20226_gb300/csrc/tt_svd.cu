@@ -204,6 +204,133 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
   }
 }
 
+// FP64 one-sided Jacobi of a factor of at most 64 x 64 in one CTA of 8 warps, round-robin
+// ordering.  Each round runs in three phases: every warp forms the three dot products of
+// its (up to four) pairs, rows over lanes, keeping the columns in registers; warp 0 derives
+// the rotations of all the round's pairs at once, one pair per lane, so the divisions and
+// square roots (~60 FP64 instructions) are issued once per round rather than once per
+// pair - at 2 FP64 lanes per clock per SM they dominated small factors; the warps apply
+// them.  The arithmetic of each pair is that of rotate_pair.
+constexpr int kSmallJacobi = 64;
+
+__global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, int ncol, int ldx, double tol,
+                                                           double negl_scale, const double* norm, int max_sweeps,
+                                                           unsigned* rot, unsigned* status, int* sweeps_out) {
+  constexpr int TPL = kSmallJacobi / 32, PPW = kSmallJacobi / 2 / 8;
+  __shared__ double s_abg[32][3];
+  __shared__ double s_cs[32][2];
+  __shared__ int s_do[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double nl = negl_scale > 0.0 ? negl_scale * __ldcg(norm) : 0.0;
+  const double negl = nl * nl;
+  const int N = ncol + (ncol & 1), npairs = N / 2;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    unsigned nrot = 0;  // warp 0, lane 0
+    for (int rnd = 0; rnd < N - 1; ++rnd) {
+      double ra[PPW][TPL], rb[PPW][TPL];
+      // ---- phase A: dot products of this warp's pairs
+#pragma unroll
+      for (int j = 0; j < PPW; ++j) {
+        const int q = warp + 8 * j;
+        int a = 0, b = 0;
+        if (q < npairs) {
+          a = q == 0 ? rnd : (rnd + q) % (N - 1);
+          b = q == 0 ? N - 1 : (rnd - q + N - 1) % (N - 1);
+          if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+          }
+        }
+        double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+          ra[j][u] = rb[j][u] = 0.0;
+          if (q < npairs && b < ncol && 32 * u < nrow) {
+            const int i = lane + 32 * u;
+            if (i < nrow) {
+              ra[j][u] = X[i + (int64_t)a * ldx];
+              rb[j][u] = X[i + (int64_t)b * ldx];
+            }
+            al = fma(ra[j][u], ra[j][u], al);
+            be = fma(rb[j][u], rb[j][u], be);
+            ga = fma(ra[j][u], rb[j][u], ga);
+          }
+        }
+        if (q < npairs) {
+          const double v = warp_sum3_split(al, be, ga, lane);
+          if ((lane & 7) == 0 && lane < 24) s_abg[q][lane >> 3] = v;
+        }
+      }
+      __syncthreads();
+      // ---- phase B: the rotations, one pair per lane of warp 0
+      if (warp == 0) {
+        int doit = 0;
+        double c = 1.0, sn = 0.0;
+        if (lane < npairs) {
+          int a = lane == 0 ? rnd : (rnd + lane) % (N - 1);
+          int b = lane == 0 ? N - 1 : (rnd - lane + N - 1) % (N - 1);
+          if (a > b) b = a;  // only b can be the padding column N - 1
+          const double al = s_abg[lane][0], be = s_abg[lane][1], ga = s_abg[lane][2];
+          if (b < ncol && !(al < negl && be < negl) && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double tn = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                                   : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + tn * tn);
+            sn = c * tn;
+            doit = sn != 0.0;
+          }
+          s_cs[lane][0] = c;
+          s_cs[lane][1] = sn;
+          s_do[lane] = doit;
+        }
+        nrot += __popc(__ballot_sync(0xffffffffu, doit));
+      }
+      __syncthreads();
+      // ---- phase C: apply
+#pragma unroll
+      for (int j = 0; j < PPW; ++j) {
+        const int q = warp + 8 * j;
+        if (q < npairs && s_do[q]) {
+          int a = q == 0 ? rnd : (rnd + q) % (N - 1);
+          int b = q == 0 ? N - 1 : (rnd - q + N - 1) % (N - 1);
+          if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+          }
+          const double c = s_cs[q][0], sn = s_cs[q][1];
+#pragma unroll
+          for (int u = 0; u < TPL; ++u) {
+            if (32 * u < nrow) {
+              const int i = lane + 32 * u;
+              if (i < nrow) {
+                X[i + (int64_t)a * ldx] = c * ra[j][u] - sn * rb[j][u];
+                X[i + (int64_t)b * ldx] = sn * ra[j][u] + c * rb[j][u];
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    __shared__ unsigned s_nrot;
+    if (threadIdx.x == 0) {
+      s_nrot = nrot;
+      if (nrot) atomicAdd(rot + sweep, nrot);
+    }
+    __syncthreads();
+    converged = s_nrot == 0u;
+    __syncthreads();  // s_nrot is read before the next sweep overwrites it
+  }
+  if (threadIdx.x == 0) {
+    *sweeps_out = sweep;
+    if (!converged) atomicOr(status, (unsigned)ST_NONCONVERGED);
+  }
+}
+
 // The same FP64 Jacobi with one CTA of WPP warps per pair: the rows of the pair are split
 // over the warps (shorter dependent FMA chains, WPP times the warps per SM), the partial
 // sums are combined in shared memory in a fixed order, and one thread derives the rotation
@@ -320,9 +447,11 @@ __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nro
             }
           }
         }
-        __syncthreads();  // every warp's stores (and reads of red / s_cs) precede the release
+        // every warp's stores (and reads of red / s_cs) precede the release: the CTA barrier
+        // orders them before thread 0's st.release.gpu, and a release is cumulative, so a CTA
+        // that acquires the epoch sees the rotated columns (no separate fence.sc needed)
+        __syncthreads();
         if (threadIdx.x == 0) {
-          __threadfence();
           st_release_u32(epoch + a, t + 1);
           if (real_b) st_release_u32(epoch + b, t + 1);
         }
@@ -680,6 +809,53 @@ __device__ __forceinline__ void rinv_colnorm_body(const double* R, int p, int ld
   if (lane == 0) colsq[j] = nrm2;
 }
 
+// The same column norms, column-oriented: one warp per column j forms z = R^{-1} e_j by
+//   for i = j .. 0:  z_i = b_i / R_ii;  b_k -= z_i R_ki  (k < i)
+// with the right-hand side b in registers (b_k in lane k % 32, slot k / 32), so a step is
+// one broadcast, one multiply and one FMA per slot - no warp reduction and no division
+// on the critical path (the row-oriented form above needs both, and reads a row of the
+// column-major R per step).  The CTA's warps share 32-column blocks of R (with the
+// inverses of their diagonal) staged in shared memory.  p <= 32 KS.
+constexpr int kRinvWarps = 4;
+
+template <int KS>
+__global__ void __launch_bounds__(32 * kRinvWarps) rinv_colnorm_cols_kernel(const double* __restrict__ R, int p,
+                                                                            int ldr, double* __restrict__ colsq) {
+  extern __shared__ double rs[];  // rows [0, c0 + 32) x 32 columns (ld = rows), then 32 inverse diagonals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * kRinvWarps + warp;
+  const int jmax = min(p - 1, blockIdx.x * kRinvWarps + kRinvWarps - 1);
+  double b[KS];
+#pragma unroll
+  for (int q = 0; q < KS; ++q) b[q] = (32 * q + lane == j) ? 1.0 : 0.0;
+  double nrm2 = 0.0;
+#pragma unroll
+  for (int B = KS - 1; B >= 0; --B) {
+    if (32 * B > jmax) continue;  // CTA-uniform
+    const int c0 = 32 * B, rows = min(p, c0 + 32), nc = min(32, p - c0);
+    double* dinv = rs + (size_t)rows * 32;
+    __syncthreads();  // the previous block is consumed
+    for (int e = threadIdx.x; e < rows * nc; e += blockDim.x) {
+      const int r = e % rows, cc = e / rows;
+      rs[r + cc * rows] = __ldg(R + r + (int64_t)(c0 + cc) * ldr);
+    }
+    if (threadIdx.x < nc) dinv[threadIdx.x] = 1.0 / __ldg(R + (c0 + threadIdx.x) + (int64_t)(c0 + threadIdx.x) * ldr);
+    __syncthreads();
+    if (j < p) {
+      const int top = min(31, j - c0);  // steps i = c0 + ii, ii = top .. 0 (i <= j)
+      for (int ii = top; ii >= 0; --ii) {
+        const double zi = __shfl_sync(0xffffffffu, b[B], ii) * dinv[ii];
+        nrm2 = fma(zi, zi, nrm2);
+        const double* col = rs + ii * rows;  // column c0 + ii of R, rows [0, c0 + 32)
+#pragma unroll
+        for (int q = 0; q < B; ++q) b[q] = fma(-zi, col[32 * q + lane], b[q]);
+        if (lane < ii) b[B] = fma(-zi, col[c0 + lane], b[B]);
+      }
+    }
+  }
+  if (j < p && lane == 0) colsq[j] = nrm2;
+}
+
 __global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int p, int ldr,
                                                            double* colsq) {
   rinv_colnorm_body(R, p, ldr, colsq, blockIdx.x);
@@ -981,6 +1157,12 @@ template <int NT, int TPL>
 int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, double negl_scale,
                   int max_sweeps) {
   const int npairs = (ncol + 1) / 2;
+  if (ncol <= kSmallJacobi && nrow <= kSmallJacobi) {
+    jacobi_small_kernel<<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, negl_scale, w.norm, max_sweeps, w.rot,
+                                          w.status, w.sweeps);
+    TT_LAUNCH_CHECK();
+    return TT_OK;
+  }
   if (ncol <= 48) {
     jacobi_kernel<256, TPL, false><<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, negl_scale, w.norm,
                                                       max_sweeps, w.bar, w.rot, w.status, w.sweeps, nullptr);
@@ -1063,7 +1245,28 @@ int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ld
                                        200 * 1024));
     configured = dev;
   }
-  rinv_colnorm_kernel<<<(unsigned)ceil_div(p, 8), 256, smem, s>>>(R, p, ldr, w.sigma);
+  if (p <= 512) {
+    static int configured_cols = -1;
+    if (configured_cols != dev) {
+      TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024));
+      TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024));
+      TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024));
+      configured_cols = dev;
+    }
+    const size_t smem_c = ((size_t)p * 32 + 32) * sizeof(double);
+    const unsigned grid = (unsigned)ceil_div(p, kRinvWarps);
+    if (p <= 128)
+      rinv_colnorm_cols_kernel<4><<<grid, 32 * kRinvWarps, smem_c, s>>>(R, p, ldr, w.sigma);
+    else if (p <= 256)
+      rinv_colnorm_cols_kernel<8><<<grid, 32 * kRinvWarps, smem_c, s>>>(R, p, ldr, w.sigma);
+    else
+      rinv_colnorm_cols_kernel<16><<<grid, 32 * kRinvWarps, smem_c, s>>>(R, p, ldr, w.sigma);
+  } else {
+    rinv_colnorm_kernel<<<(unsigned)ceil_div(p, 8), 256, smem, s>>>(R, p, ldr, w.sigma);
+  }
   TT_LAUNCH_CHECK();
   certify_kernel<<<1, 1024, 0, s>>>(R, p, ldr, w.sigma, w.norm, delta_scale, unit, rel_floor, w.rank);
   TT_LAUNCH_CHECK();
