@@ -243,6 +243,9 @@ def run_ours(args):
         extra["batched"] = bench_batched(tt, dev, Wm, n_tt=args.batch_trains, rank=rank, world=world)
         extra["eval"] = bench_eval(tt, dev)
         extra["small_1d"] = bench_small(tt, dev)
+        extra["laplacian3d_rank256"] = bench_large(tt, dev, "laplacian3d")
+        if args.large:
+            extra["hadamard_square_rank64"] = bench_large(tt, dev, "hadamard")
 
     # ---- end to end: pinned host cores in, rounded cores out, through the public API
     xh = [torch.as_tensor(c).pin_memory() for c in x_np]
@@ -344,7 +347,7 @@ def bench_batched(tt, dev, warm, n_tt=512, nstreams=5, repeats=3, rank=0, world=
     from oracle import core as ocore
     from paper_2602_20226_gb300 import inputs
     from paper_2602_20226_gb300.flops import apply_flops, round_flops
-    from paper_2602_20226_gb300.shard import lpt_partition
+    from paper_2602_20226_gb300.shard import aggregate_throughput, lpt_partition
 
     all_shapes = inputs.batch_shapes(4, n_tt)
     mine = lpt_partition(all_shapes, world)[rank]
@@ -372,11 +375,7 @@ def bench_batched(tt, dev, warm, n_tt=512, nstreams=5, repeats=3, rank=0, world=
             yr = [a * b for a, b in zip(w.ranks, x.ranks)]
             flops += apply_flops(w.ranks, x.ranks, x.dims) + round_flops(yr, o.ranks, x.dims)["total"]
         if world > 1:
-            t = torch.tensor([sec, flops], dtype=torch.float64, device=dev)
-            mx = t.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            sec, flops = float(mx[0].item()), float(t[1].item())
+            flops, sec = aggregate_throughput(flops, sec, device=dev)
         res[form] = {"value": round(flops / sec / 1e9, 3), "unit": "GFLOP/s", "seconds": round(sec, 3),
                      "seconds_each": [round(v, 3) for v in secs], "nominal_flops": flops}
         outs_by_form[form] = outs
@@ -453,6 +452,53 @@ def bench_eval(tt, dev, n=1 << 20, L=40, r=64):
                                  "and per-site sums over 2048-sample slices, FP64 across slices"}}
 
 
+def bench_large(tt, dev, case):
+    """One of the two large configurations, one call each (apply or Hadamard product, then
+    tt_round), host-timed with a device synchronisation on both sides:
+      laplacian3d: 3D quantics TT (3 x 16 bits interleaved, L = 48), rank 256, FP32 cores,
+          3D Dirichlet Laplacian MPO (rank 7, bond ranks 1792), mixed rounding at 1e-6;
+      hadamard: 2D (2 x 20 bits, L = 40), rank 64, FP64, x (.) x (bond ranks 4096), FP64
+          rounding at 1e-8.
+    Checked on the GPU alone: the rounding bound ||z - y|| <= eps ||y|| from FP64 inner
+    products (laplacian3d; at 1e-8 that difference is below the resolution of inner products)
+    and the closed-form rank bound r (r + 1) / 2 of x (.) x.  The same workloads at L = 24 are
+    checked against stored oracle values in the GPU tests."""
+    import torch
+
+    from paper_2602_20226_gb300 import inputs, qtt
+    from paper_2602_20226_gb300.flops import apply_flops, hadamard_flops, round_flops
+
+    if case == "laplacian3d":
+        L, r, eps = 48, 256, 1e-6
+        X = tt.TT.from_numpy([c.astype(np.float32) for c in inputs.random_tt(2, L, 2, r)], device=dev,
+                             dtype=torch.float32)
+        W = tt.MPO.from_numpy(qtt.laplacian_mpo(3, L // 3), device=dev, dtype=torch.float32)
+    else:
+        L, r, eps = 40, 64, 1e-8
+        X = tt.TT.from_numpy(inputs.random_tt(2, L, 2, r), device=dev)
+        W = None
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    Y = tt.tt_apply_mpo(W, X) if W is not None else tt.tt_hadamard(X, X)
+    Z, _ = tt.tt_round(Y, eps)
+    torch.cuda.synchronize(dev)
+    sec = time.perf_counter() - t0
+    fl = (apply_flops([int(v) for v in W.ranks], X.ranks, X.dims) if W is not None
+          else hadamard_flops(X.ranks, X.ranks, X.dims)) + round_flops(Y.ranks, Z.ranks, X.dims)["total"]
+    out = {"seconds": round(sec, 3), "value": round(fl / sec / 1e9, 2), "unit": "GFLOP/s",
+           "ranks_in_max": max(Y.ranks), "ranks_out_max": max(Z.ranks), "eps": eps}
+    if W is not None:
+        out["workload"] = ("3D quantics TT L=48 (3x16 bits), rank 256, FP32 cores, 3D Dirichlet Laplacian MPO "
+                           "rank 7, apply + tt_round mixed eps=1e-6 (one host-timed call)")
+        zz, yy, zy = tt.tt_inner(Z, Z), tt.tt_inner(Y, Y), tt.tt_inner(Z, Y)
+        out["rounding_rel_err"] = float(np.sqrt(max(zz + yy - 2.0 * zy, 0.0) / yy))
+    else:
+        out["workload"] = ("2D quantics TT L=40 (2x20 bits), rank 64, FP64, Hadamard square x*x (ranks 4096) "
+                           "+ tt_round eps=1e-8 (one host-timed call)")
+        out["closed_form_rank_bound"] = r * (r + 1) // 2
+    return out
+
+
 def bench_small(tt, dev, reps=50):
     """The small 1D workload: L = 10, rank 8, second-difference MPO (rank 3), eps = 1e-10,
     FP64 - latency of one apply + round (launch- and synchronisation-bound)."""
@@ -494,9 +540,38 @@ def cpu_baseline(x_np, W_np, eps, flops_step, repeats=2):
         ocore.round_tt(y, eps)
         times.append(time.perf_counter() - t0)
     s = float(np.mean(times))
-    return {"value": round(flops_step / s / 1e9, 4), "unit": "GFLOP/s", "cores": len(os.sched_getaffinity(0)),
-            "kind": "oracle", "sample": f"{repeats} full steps (apply + round of the L=40 rank-64 TT), "
-                                        f"{s:.2f} s each, numpy/LAPACK FP64"}
+    out = {"value": round(flops_step / s / 1e9, 4), "unit": "GFLOP/s", "cores": len(os.sched_getaffinity(0)),
+           "kind": "oracle", "sample": f"{repeats} full steps (apply + round of the L=40 rank-64 TT), "
+                                       f"{s:.2f} s each, numpy/LAPACK FP64"}
+    s1 = _oracle_step_seconds_one_thread()
+    if s1 is not None:
+        out["one_thread"] = {"value": round(flops_step / s1 / 1e9, 4), "unit": "GFLOP/s", "cores": 1,
+                             "sample": f"1 full step in a child process with one BLAS/OpenMP thread, {s1:.2f} s"}
+    return out
+
+
+def _oracle_step_seconds_one_thread():
+    """One oracle step in a fresh child interpreter whose BLAS and OpenMP pools have one thread."""
+    code = (
+        "import time, sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from oracle import core, structured\n"
+        "from paper_2602_20226_gb300 import inputs\n"
+        f"w = {dict(WORKLOAD)!r}\n"
+        "x = inputs.random_tt(w['seed'], w['L'], 2, w['rank'])\n"
+        "W = structured.laplacian_mpo(w['n_dims'], w['bits'])\n"
+        "t0 = time.perf_counter()\n"
+        "core.round_tt(core.apply_mpo(W, x), w['eps'])\n"
+        "print(time.perf_counter() - t0)\n"
+    )
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
 
 
 def run_reference(args):
@@ -545,6 +620,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--large", action="store_true",
+                    help="also time x (.) x of the rank-64 2D train (bond ranks 4096; ~100 s)")
     ap.add_argument("--batch-trains", type=int, default=512,
                     help="trains in the secondary batched workload (default: the full batch of 512)")
     args = ap.parse_args()

@@ -74,3 +74,17 @@ def allreduce_core_grads(grads, group=None) -> None:
         n = g.numel()
         g.copy_(flat[off:off + n].view_as(g))
         off += n
+
+
+def aggregate_throughput(units: float, seconds: float, device=None, group=None) -> tuple[float, float]:
+    """Whole-job throughput of a weakly scaled run: the units all ranks processed and the
+    slowest rank's time (torch.distributed must be initialised).  Returns (total units,
+    max seconds); the job's rate is their quotient."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(units), float(seconds)], dtype=torch.float64, device=device)
+    tot = t.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(tot[0].item()), float(t[1].item())

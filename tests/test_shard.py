@@ -120,3 +120,32 @@ def test_two_gloo_ranks_sum_the_fit_gradient():
     ref = grad.fit_loss_grad(x, dg, inputs.fit_targets(dg, 6))
     for a, b in zip(got, ref):
         assert np.abs(a - b).max() <= 1e-14 * max(1.0, np.abs(b).max())
+
+
+def _agg_rank_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2602_20226_gb300.shard import aggregate_throughput
+
+    # rank r processed 10 (r + 1) units in 2 + 3 r seconds
+    got = aggregate_throughput(10.0 * (rank + 1), 2.0 + 3.0 * rank)
+    q.put((rank, got))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_throughput():
+    """The bench's whole-job rate: units summed over the ranks, time of the slowest rank,
+    the same on every rank."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_agg_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got[0] == got[1] == (30.0, 5.0)
