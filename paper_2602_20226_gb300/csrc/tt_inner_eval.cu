@@ -75,6 +75,65 @@ __host__ __device__ constexpr int eval_row_pad(int r1) {
   return sizeof(T) == 4 ? ((r1 + 3) & ~3) + 4 : ((r1 + 1) & ~1) + 2;
 }
 
+// Copies the CTA's nb digit bytes into shared memory: 16-byte loads when the source is
+// 16-byte aligned, all of a thread's loads issued before its stores.
+__device__ __forceinline__ void stage_digits(const uint8_t* __restrict__ src, long long nb, uint8_t* __restrict__ dst) {
+  const int S = blockDim.x;
+  long long done = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    const long long n16 = nb / 16;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (long long base = threadIdx.x; base < n16; base += (long long)S * 4) {
+      uint4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long q = base + (long long)u * S;
+        if (q < n16) v[u] = __ldg(s4 + q);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long q = base + (long long)u * S;
+        if (q < n16) d4[q] = v[u];
+      }
+    }
+    done = n16 * 16;
+  }
+  for (long long e = done + threadIdx.x; e < nb; e += S) dst[e] = src[e];
+}
+
+// Copies core G (rows = r0 d rows of r1 values, row-major) into shared memory: row-major with
+// row stride ldst, or transposed (row (c d + i) holds G[:, i, c], stride ldst).  Each thread
+// issues U loads before its first store, so staging a core costs a few L2 latencies rather
+// than one per element a thread copies.
+template <typename T, int U>
+__device__ __forceinline__ void stage_core(const T* __restrict__ G, int r0, int d, int r1, T* __restrict__ stage,
+                                           int ldst, bool transpose) {
+  const int total = r0 * d * r1;
+  const int S = blockDim.x;
+  for (int base = threadIdx.x; base < total; base += S * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * S;
+      v[u] = e < total ? __ldg(G + e) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * S;
+      if (e < total) {
+        const int row = e / r1, c = e - row * r1;
+        if (!transpose) {
+          stage[row * ldst + c] = v[u];
+        } else {
+          const int a = row / d, i = row - a * d;
+          stage[(c * d + i) * ldst + a] = v[u];
+        }
+      }
+    }
+  }
+}
+
 template <typename T, int JB>
 __global__ void eval_staged_kernel(EvalParams<T> P, const uint8_t* __restrict__ digits, long long n,
                                    T* __restrict__ values, unsigned* status, int stage_elems) {
@@ -91,7 +150,7 @@ __global__ void eval_staged_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
   {
     const long long nb = (long long)min((long long)S, n - s0) * P.L;
     const uint8_t* src = digits + s0 * P.L;
-    for (long long e = tid; e < nb; e += S) dg[e] = src[e];
+    stage_digits(src, nb, dg);
   }
   cur[tid] = T(1);
   constexpr int VW = 16 / sizeof(T);  // elements per 16-byte load
@@ -100,14 +159,7 @@ __global__ void eval_staged_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
     const int r0 = P.r[k], r1 = P.r[k + 1], d = P.d[k];
     const int r1p = eval_row_pad<T>(r1);
     __syncthreads();  // the previous site is done with the stage; digits are staged
-    {
-      const T* G = P.g[k];
-      const int rows = r0 * d;
-      for (int e = tid; e < rows * r1; e += S) {
-        const int row = e / r1, c = e - row * r1;
-        stage[row * r1p + c] = G[e];
-      }
-    }
+    stage_core<T, 16 / (sizeof(T) / 4)>(P.g[k], r0, d, r1, stage, r1p, false);
     __syncthreads();
     int dig = active ? (int)dg[tid * P.L + k] : 0;
     if (dig >= d) {
@@ -191,7 +243,7 @@ __global__ void eval_states_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
   {
     const long long nb = (long long)min((long long)S, n - s0) * P.L;
     const uint8_t* src = digits + s0 * P.L;
-    for (long long e = tid; e < nb; e += S) dg[e] = src[e];
+    stage_digits(src, nb, dg);
   }
   cur[tid] = T(1);
   constexpr int VW = 16 / sizeof(T);
@@ -209,19 +261,7 @@ __global__ void eval_states_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
     if (step == L - 1) break;  // the full product is not needed
     const int routp = eval_row_pad<T>(rout);
     __syncthreads();
-    {
-      const T* G = P.g[k];
-      const int total = r0 * d * r1;
-      for (int e = tid; e < total; e += S) {
-        const int row = e / r1, c = e - row * r1;  // row = a d + i, c = b
-        if (!suffix) {
-          stage[row * routp + c] = G[e];
-        } else {
-          const int a = row / d, i = row - a * d;
-          stage[(c * d + i) * routp + a] = G[e];
-        }
-      }
-    }
+    stage_core<T, 16 / (sizeof(T) / 4)>(P.g[k], r0, d, r1, stage, routp, suffix);
     __syncthreads();
     int dig = active ? (int)dg[tid * L + k] : 0;
     if (dig >= d) dig = 0;  // the accumulation skips such samples at this site
@@ -314,16 +354,27 @@ __global__ void __launch_bounds__(128) eval_bwd_accum_kernel(EvalParams<T> P, Si
   for (long long t0 = sb; t0 < se; t0 += kAccK) {
     const int kt = (int)min((long long)kAccK, se - t0);
     __syncthreads();  // the previous tile is consumed
-    // stage p (times w) and q: element e -> (row j, sample s), coalesced along samples
-    for (int e = tid; e < kAccTile * kAccK; e += 128) {
-      const int j = e / kAccK, s = e - j * kAccK;
-      T pv = T(0), qv = T(0);
-      if (s < kt) {
-        if (a0 + j < r0) pv = Pk[(long long)(a0 + j) * C + t0 + s] * w[t0 + s];
-        if (b0 + j < r1) qv = Qk[(long long)(b0 + j) * C + t0 + s];
+    // stage p (times w) and q: element e -> (row j, sample s), coalesced along samples; a
+    // thread issues the loads of four elements before storing any
+    constexpr int SU = 4;
+    for (int e0 = tid; e0 < kAccTile * kAccK; e0 += 128 * SU) {
+      T pv[SU], qv[SU], wv[SU];
+#pragma unroll
+      for (int u = 0; u < SU; ++u) {
+        const int e = e0 + 128 * u, j = e / kAccK, s = e - j * kAccK;
+        pv[u] = qv[u] = wv[u] = T(0);
+        if (s < kt) {
+          if (a0 + j < r0) pv[u] = __ldg(Pk + (long long)(a0 + j) * C + t0 + s);
+          if (b0 + j < r1) qv[u] = __ldg(Qk + (long long)(b0 + j) * C + t0 + s);
+          wv[u] = __ldg(w + t0 + s);
+        }
       }
-      Ps[s][j] = pv;
-      Qs[s][j] = qv;
+#pragma unroll
+      for (int u = 0; u < SU; ++u) {
+        const int e = e0 + 128 * u, j = e / kAccK, s = e - j * kAccK;
+        Ps[s][j] = pv[u] * wv[u];
+        Qs[s][j] = qv[u];
+      }
     }
     if (tid < 32) {
       const int dgt = tid < kt ? (int)digits[(t0 + tid) * L + k] : -1;

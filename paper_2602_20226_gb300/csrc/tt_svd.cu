@@ -204,6 +204,29 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
   }
 }
 
+// The rotation of one-sided Jacobi for a pair with squared norms al, be and product ga, or
+// false if the pair is left alone.  tan(theta) is the smaller root of t^2 + 2 zeta t - 1 = 0,
+// zeta = (be - al) / (2 ga), written as t = sgn(d) 2 ga / (|d| + sqrt(d^2 + 4 ga^2)) with
+// d = be - al: one square root, one division and one reciprocal square root on the
+// dependent chain (the zeta form has three divisions and three square roots).  The sums are
+// first scaled by a power of two (exact), so d^2 + 4 ga^2 can neither overflow nor underflow,
+// and the acceptance test |ga| > tol sqrt(al be) is taken as ga^2 > tol^2 al be on them.
+__device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga, double tol, double negl, double& c,
+                                                double& sn) {
+  if ((al < negl && be < negl) || ga == 0.0) return false;
+  const int e = ilogb(fmax(al, be));
+  al = scalbn(al, -e);
+  be = scalbn(be, -e);
+  ga = scalbn(ga, -e);
+  if (!(ga * ga > (tol * tol) * (al * be))) return false;
+  const double d = be - al;
+  const double h = sqrt(fma(d, d, 4.0 * ga * ga));
+  const double t = copysign(1.0, d) * (2.0 * ga) / (fabs(d) + h);
+  c = rsqrt(fma(t, t, 1.0));
+  sn = c * t;
+  return sn != 0.0;
+}
+
 // FP64 one-sided Jacobi of a factor of at most 64 x 64 in one CTA of 8 warps, round-robin
 // ordering.  Each round runs in three phases: every warp forms the three dot products of
 // its (up to four) pairs, rows over lanes, keeping the columns in registers; warp 0 derives
@@ -273,14 +296,10 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, 
           int a = lane == 0 ? rnd : (rnd + lane) % (N - 1);
           int b = lane == 0 ? N - 1 : (rnd - lane + N - 1) % (N - 1);
           if (a > b) b = a;  // only b can be the padding column N - 1
-          const double al = s_abg[lane][0], be = s_abg[lane][1], ga = s_abg[lane][2];
-          if (b < ncol && !(al < negl && be < negl) && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-            const double zeta = (be - al) / (2.0 * ga);
-            const double tn = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                                   : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + tn * tn);
-            sn = c * tn;
-            doit = sn != 0.0;
+          if (b < ncol) doit = jacobi_rotation(s_abg[lane][0], s_abg[lane][1], s_abg[lane][2], tol, negl, c, sn);
+          if (!doit) {
+            c = 1.0;
+            sn = 0.0;
           }
           s_cs[lane][0] = c;
           s_cs[lane][1] = sn;
@@ -417,16 +436,8 @@ __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nro
               be += red[w][1];
               ga += red[w][2];
             }
-            bool doit = !(al < negl && be < negl) && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be);
             double c = 1.0, sn = 0.0;
-            if (doit) {
-              const double zeta = (be - al) / (2.0 * ga);
-              const double tn = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                                     : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-              c = 1.0 / sqrt(1.0 + tn * tn);
-              sn = c * tn;
-              doit = sn != 0.0;
-            }
+            const bool doit = jacobi_rotation(al, be, ga, tol, negl, c, sn);
             s_cs[0] = c;
             s_cs[1] = sn;
             s_doit = doit;
