@@ -358,13 +358,30 @@ __device__ __forceinline__ void reflector_body(const T* __restrict__ V, int ldv,
   float ah = 0.0f, al = 0.0f;
   for (int l0 = 0; l0 < mr; l0 += RCH) {
     const int rows = min(RCH, mr - l0);
-    for (int e = tid; e < RCH * NB; e += RT) {
-      const int r = e % RCH, c = e / RCH;
-      Vs[r][c] = (r < rows && c < jb) ? V[(int64_t)c * ldv + l0 + r] : T(0);
-    }
-    for (int e = tid; e < RCH * RNC; e += RT) {
-      const int r = e % RCH, c = e / RCH;
-      Xs[r][c] = (r < rows && c < ncol) ? X[(int64_t)(c0 + c) * ldx + l0 + r] : T(0);
+    {
+      // all of a thread's loads of the chunk are issued before its stores
+      constexpr int UV = RCH * NB / RT, UX = (RCH * RNC + RT - 1) / RT;
+      T vv[UV], xv[UX];
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const int e = tid + u * RT, r = e % RCH, c = e / RCH;
+        vv[u] = (r < rows && c < jb) ? V[(int64_t)c * ldv + l0 + r] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < UX; ++u) {
+        const int e = tid + u * RT, r = e % RCH, c = e / RCH;
+        xv[u] = (e < RCH * RNC && r < rows && c < ncol) ? X[(int64_t)(c0 + c) * ldx + l0 + r] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const int e = tid + u * RT;
+        Vs[e % RCH][e / RCH] = vv[u];
+      }
+#pragma unroll
+      for (int u = 0; u < UX; ++u) {
+        const int e = tid + u * RT;
+        if (e < RCH * RNC) Xs[e % RCH][e / RCH] = xv[u];
+      }
     }
     __syncthreads();
     if constexpr (kMixed) {
@@ -412,29 +429,40 @@ __device__ __forceinline__ void reflector_body(const T* __restrict__ V, int ldv,
     }
   }
   __syncthreads();
-  // ---- X -= V W2, one thread per (row, column); V read from L2 (coalesced along rows)
-  for (int e = tid; e < mr * RNC; e += RT) {
-    const int l = e % mr, jj = e / mr;
-    if (jj >= ncol) continue;
-    T* px = X + (int64_t)(c0 + jj) * ldx + l;
-    if constexpr (kMixed) {
-      float sh = 0.0f, sl = 0.0f;
-      for (int r = 0; r < jb; ++r) {
-        const float a = V[(int64_t)r * ldv + l];
-        const float wh = W2h[r][jj];
-        const float p = __fmul_rn(a, wh);
-        const float er = __fmaf_rn(a, wh, -p);
-        const float s = __fadd_rn(sh, p);
-        const float z = __fsub_rn(s, sh);
-        const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
-        sh = s;
-        sl = __fadd_rn(sl, __fadd_rn(err, __fmaf_rn(a, W2l[r][jj], er)));
+  // ---- X -= V W2, one thread per row and all RNC columns: the jb entries of the row of V
+  // are loaded together (coalesced along rows) and each feeds RNC products
+  for (int l = tid; l < mr; l += RT) {
+    T vr[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) vr[r] = r < jb ? V[(int64_t)r * ldv + l] : T(0);
+#pragma unroll
+    for (int jj = 0; jj < RNC; ++jj) {
+      if (jj >= ncol) break;
+      T* px = X + (int64_t)(c0 + jj) * ldx + l;
+      if constexpr (kMixed) {
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+          if (r < jb) {
+            const float a = vr[r];
+            const float wh = W2h[r][jj];
+            const float p = __fmul_rn(a, wh);
+            const float er = __fmaf_rn(a, wh, -p);
+            const float s = __fadd_rn(sh, p);
+            const float z = __fsub_rn(s, sh);
+            const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+            sh = s;
+            sl = __fadd_rn(sl, __fadd_rn(err, __fmaf_rn(a, W2l[r][jj], er)));
+          }
+        }
+        *px = (float)((double)*px - ((double)sh + (double)sl));
+      } else {
+        double v = 0.0;
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+          if (r < jb) v = fma((double)vr[r], W2[r][jj], v);
+        *px = (T)((double)*px - v);
       }
-      *px = (float)((double)*px - ((double)sh + (double)sl));
-    } else {
-      double v = 0.0;
-      for (int r = 0; r < jb; ++r) v = fma((double)V[(int64_t)r * ldv + l], W2[r][jj], v);
-      *px = (T)((double)*px - v);
     }
   }
 }
