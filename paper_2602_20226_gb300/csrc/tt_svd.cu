@@ -228,12 +228,12 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga,
 }
 
 // FP64 one-sided Jacobi of a factor of at most 64 x 64 in one CTA of 8 warps, round-robin
-// ordering.  Each round runs in three phases: every warp forms the three dot products of
-// its (up to four) pairs, rows over lanes, keeping the columns in registers; warp 0 derives
-// the rotations of all the round's pairs at once, one pair per lane, so the divisions and
-// square roots (~60 FP64 instructions) are issued once per round rather than once per
-// pair - at 2 FP64 lanes per clock per SM they dominated small factors; the warps apply
-// them.  The arithmetic of each pair is that of rotate_pair.
+// ordering, the factor held in shared memory for the whole run.  Each round runs in three
+// phases: every warp forms the three dot products of its (up to four) pairs, rows over
+// lanes, keeping the columns in registers; warp 0 derives the rotations of all the round's
+// pairs at once, one pair per lane (jacobi_rotation), so the square roots and divisions are
+// issued once per round rather than once per pair - at 2 FP64 lanes per clock per SM they
+// dominated small factors; the warps apply them.
 constexpr int kSmallJacobi = 64;
 
 __global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, int ncol, int ldx, double tol,
@@ -243,7 +243,13 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, 
   __shared__ double s_abg[32][3];
   __shared__ double s_cs[32][2];
   __shared__ int s_do[32];
+  extern __shared__ double Xs[];  // the factor, column-major, ld nrow: it stays on chip
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+    const int i = e % nrow, col = e / nrow;
+    Xs[e] = X[i + (int64_t)col * ldx];
+  }
+  __syncthreads();
   const double nl = negl_scale > 0.0 ? negl_scale * __ldcg(norm) : 0.0;
   const double negl = nl * nl;
   const int N = ncol + (ncol & 1), npairs = N / 2;
@@ -274,8 +280,8 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, 
           if (q < npairs && b < ncol && 32 * u < nrow) {
             const int i = lane + 32 * u;
             if (i < nrow) {
-              ra[j][u] = X[i + (int64_t)a * ldx];
-              rb[j][u] = X[i + (int64_t)b * ldx];
+              ra[j][u] = Xs[i + a * nrow];
+              rb[j][u] = Xs[i + b * nrow];
             }
             al = fma(ra[j][u], ra[j][u], al);
             be = fma(rb[j][u], rb[j][u], be);
@@ -326,8 +332,8 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, 
             if (32 * u < nrow) {
               const int i = lane + 32 * u;
               if (i < nrow) {
-                X[i + (int64_t)a * ldx] = c * ra[j][u] - sn * rb[j][u];
-                X[i + (int64_t)b * ldx] = sn * ra[j][u] + c * rb[j][u];
+                Xs[i + a * nrow] = c * ra[j][u] - sn * rb[j][u];
+                Xs[i + b * nrow] = sn * ra[j][u] + c * rb[j][u];
               }
             }
           }
@@ -343,6 +349,10 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, 
     __syncthreads();
     converged = s_nrot == 0u;
     __syncthreads();  // s_nrot is read before the next sweep overwrites it
+  }
+  for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+    const int i = e % nrow, col = e / nrow;
+    X[i + (int64_t)col * ldx] = Xs[e];
   }
   if (threadIdx.x == 0) {
     *sweeps_out = sweep;
@@ -1169,8 +1179,9 @@ int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, do
                   int max_sweeps) {
   const int npairs = (ncol + 1) / 2;
   if (ncol <= kSmallJacobi && nrow <= kSmallJacobi) {
-    jacobi_small_kernel<<<1, 256, 0, s>>>(w.X, nrow, ncol, w.ldx, tol, negl_scale, w.norm, max_sweeps, w.rot,
-                                          w.status, w.sweeps);
+    jacobi_small_kernel<<<1, 256, (size_t)nrow * ncol * sizeof(double), s>>>(w.X, nrow, ncol, w.ldx, tol, negl_scale,
+                                                                            w.norm, max_sweeps, w.rot, w.status,
+                                                                            w.sweeps);
     TT_LAUNCH_CHECK();
     return TT_OK;
   }
