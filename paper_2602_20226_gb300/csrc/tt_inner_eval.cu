@@ -134,15 +134,18 @@ __device__ __forceinline__ void stage_core(const T* __restrict__ G, int r0, int 
   }
 }
 
-template <typename T, int JB>
+// ONE: every output block fits one pass (JB >= every r_k): a thread reads only its own column
+// of the row buffer and writes it after its last read, so the row vector is updated in place
+// (one buffer: a third more CTAs per SM at rank 64).
+template <typename T, int JB, bool ONE>
 __global__ void eval_staged_kernel(EvalParams<T> P, const uint8_t* __restrict__ digits, long long n,
                                    T* __restrict__ values, unsigned* status, int stage_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = blockDim.x;
   const int tid = threadIdx.x;
   T* cur = reinterpret_cast<T*>(smem_raw);
-  T* nxt = cur + (size_t)P.rmax * S;
-  T* stage = nxt + (size_t)P.rmax * S;
+  T* nxt = ONE ? cur : cur + (size_t)P.rmax * S;
+  T* stage = (ONE ? cur : nxt) + (size_t)P.rmax * S;
   uint8_t* dg = reinterpret_cast<uint8_t*>(stage + stage_elems + JB);
   const long long s0 = (long long)blockIdx.x * S;
   const long long smp = s0 + tid;
@@ -192,9 +195,11 @@ __global__ void eval_staged_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
       for (int t = 0; t < JB; ++t)
         if (t < jn) nxt[(size_t)(j0 + t) * S + tid] = acc[t];
     }
-    T* tmp = cur;
-    cur = nxt;
-    nxt = tmp;
+    if constexpr (!ONE) {
+      T* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
   }
   if (active) values[smp] = cur[tid];
 }
@@ -226,7 +231,7 @@ __device__ __forceinline__ long long suffix_off(const int* r, int L, int k, long
 // blockIdx.y = 0: prefixes (left to right), 1: suffixes (right to left).  Same staging and
 // inner loop as eval_staged_kernel; for the suffixes the core is staged transposed
 // (row (b, i) holds G[:, i, b]), so that both directions form out = cur . stage-rows.
-template <typename T, int JB>
+template <typename T, int JB, bool ONE>
 __global__ void eval_states_kernel(EvalParams<T> P, const uint8_t* __restrict__ digits, long long n,
                                    T* __restrict__ states, long long C, int stage_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -234,8 +239,8 @@ __global__ void eval_states_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
   const int tid = threadIdx.x;
   const bool suffix = blockIdx.y == 1;
   T* cur = reinterpret_cast<T*>(smem_raw);
-  T* nxt = cur + (size_t)P.rmax * S;
-  T* stage = nxt + (size_t)P.rmax * S;
+  T* nxt = ONE ? cur : cur + (size_t)P.rmax * S;  // ONE: in place, as in eval_staged_kernel
+  T* stage = (ONE ? cur : nxt) + (size_t)P.rmax * S;
   uint8_t* dg = reinterpret_cast<uint8_t*>(stage + stage_elems + JB);
   const long long s0 = (long long)blockIdx.x * S;
   const long long smp = s0 + tid;
@@ -291,9 +296,11 @@ __global__ void eval_states_kernel(EvalParams<T> P, const uint8_t* __restrict__ 
       for (int t = 0; t < JB; ++t)
         if (t < jn) nxt[(size_t)(j0 + t) * S + tid] = acc[t];
     }
-    T* tmp = cur;
-    cur = nxt;
-    nxt = tmp;
+    if constexpr (!ONE) {
+      T* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
   }
 }
 
@@ -635,6 +642,18 @@ int inner_backward_impl(const tt_train* x, const tt_train* y, double dout, tt_tr
 }
 
 // ------------------------------------------------------------------ eval
+// Samples per CTA of the staged kernels: 128, or 64 when that keeps more warps resident (the
+// row buffers of S samples and the staged core share the SM's 227 KB of shared memory; the
+// kernels are bound by shared-memory latency, which more resident warps hide).
+inline int staged_samples(size_t per_sample_bytes, size_t fixed_bytes) {
+  auto warps = [&](int S) {
+    const size_t b = per_sample_bytes * S + fixed_bytes + 1024;
+    const int ctas = (int)std::min<size_t>(std::min<size_t>(227 * 1024 / b, 32), 2048 / S);
+    return ctas * S / 32;
+  };
+  return warps(64) > warps(128) ? 64 : 128;
+}
+
 template <typename T>
 int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values, cudaStream_t s,
               unsigned* status_dev) {
@@ -654,22 +673,42 @@ int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values,
     int stage = 1;
     for (int k = 0; k < x->L; ++k)
       stage = std::max(stage, P.r[k] * P.d[k] * eval_row_pad<T>(P.r[k + 1]));
-    constexpr int SS = 128, JB = 16;
+    static int configured_s[2] = {-1, -1};
+    int dev = 0;
+    TT_CUDA_CHECK(cudaGetDevice(&dev));
+    const int which = sizeof(T) == 8 ? 0 : 1;
+    if (configured_s[which] != dev) {
+      TT_CUDA_CHECK(cudaFuncSetAttribute(eval_staged_kernel<T, 16, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
+      if constexpr (sizeof(T) == 4)
+        TT_CUDA_CHECK(cudaFuncSetAttribute(eval_staged_kernel<T, 64, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
+      configured_s[which] = dev;
+    }
+    if constexpr (sizeof(T) == 4) {
+      // one pass per site, row vector updated in place
+      constexpr int JB = 64;
+      if (P.rmax <= JB) {
+        const int SS = staged_samples((size_t)P.rmax * sizeof(T) + x->L, (stage + JB) * sizeof(T) + 16);
+        const size_t bytes = ((size_t)P.rmax * SS + stage + JB) * sizeof(T) + (size_t)SS * x->L + 16;
+        if (bytes <= 110 * 1024) {
+          const long long blocks = ceil_div(n, SS);
+          if (blocks > 0x7fffffffLL) return fail(TT_ERR_UNSUPPORTED, "tt_eval: too many samples");
+          eval_staged_kernel<T, JB, true><<<(unsigned)blocks, SS, bytes, s>>>(P, digits, n, static_cast<T*>(values),
+                                                                               status_dev, stage);
+          TT_LAUNCH_CHECK();
+          return TT_OK;
+        }
+      }
+    }
+    constexpr int JB = 16;
+    const int SS = staged_samples(2 * (size_t)P.rmax * sizeof(T) + x->L, (stage + JB) * sizeof(T) + 16);
     const size_t bytes = (2 * (size_t)P.rmax * SS + stage + JB) * sizeof(T) + (size_t)SS * x->L + 16;
     if (bytes <= 110 * 1024) {
-      static int configured_s[2] = {-1, -1};
-      int dev = 0;
-      TT_CUDA_CHECK(cudaGetDevice(&dev));
-      const int which = sizeof(T) == 8 ? 0 : 1;
-      if (configured_s[which] != dev) {
-        TT_CUDA_CHECK(cudaFuncSetAttribute(eval_staged_kernel<T, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           110 * 1024));
-        configured_s[which] = dev;
-      }
       const long long blocks = ceil_div(n, SS);
       if (blocks > 0x7fffffffLL) return fail(TT_ERR_UNSUPPORTED, "tt_eval: too many samples");
-      eval_staged_kernel<T, JB><<<(unsigned)blocks, SS, bytes, s>>>(P, digits, n, static_cast<T*>(values),
-                                                                    status_dev, stage);
+      eval_staged_kernel<T, JB, false><<<(unsigned)blocks, SS, bytes, s>>>(P, digits, n, static_cast<T*>(values),
+                                                                           status_dev, stage);
       TT_LAUNCH_CHECK();
       return TT_OK;
     }
@@ -769,7 +808,7 @@ int eval_backward_generic(const tt_train* x, const uint8_t* digits, int64_t n, c
 
 // Staged path: shared memory of eval_states_kernel (two row buffers of S samples, the largest
 // staged core in either orientation, the CTA's digits).
-constexpr int kStatesS = 128, kStatesJB = 16;
+constexpr int kStatesJB = 16;
 constexpr size_t kStatesSmemMax = 110 * 1024;
 constexpr size_t kStateBudget = size_t(1) << 30;  // bytes of prefix + suffix states per chunk
 
@@ -783,12 +822,28 @@ int states_stage_elems(const tt_train* x) {
   return stage;
 }
 
+// FP32 trains of rank <= 64 take the one-pass, in-place form (one row buffer)
 template <typename T>
-size_t states_smem(const tt_train* x) {
+bool states_one(const tt_train* x) {
   int rmax = 1;
   for (int k = 0; k <= x->L; ++k) rmax = std::max<int>(rmax, (int)x->ranks[k]);
-  return (2 * (size_t)rmax * kStatesS + states_stage_elems<T>(x) + kStatesJB) * sizeof(T) +
-         (size_t)kStatesS * x->L + 16;
+  return sizeof(T) == 4 && rmax <= 64;
+}
+
+template <typename T>
+int states_samples(const tt_train* x) {
+  int rmax = 1;
+  for (int k = 0; k <= x->L; ++k) rmax = std::max<int>(rmax, (int)x->ranks[k]);
+  const int nbuf = states_one<T>(x) ? 1 : 2, jb = states_one<T>(x) ? 64 : kStatesJB;
+  return staged_samples(nbuf * (size_t)rmax * sizeof(T) + x->L, (states_stage_elems<T>(x) + jb) * sizeof(T) + 16);
+}
+
+template <typename T>
+size_t states_smem(const tt_train* x, int S) {
+  int rmax = 1;
+  for (int k = 0; k <= x->L; ++k) rmax = std::max<int>(rmax, (int)x->ranks[k]);
+  const int nbuf = states_one<T>(x) ? 1 : 2, jb = states_one<T>(x) ? 64 : kStatesJB;
+  return (nbuf * (size_t)rmax * S + states_stage_elems<T>(x) + jb) * sizeof(T) + (size_t)S * x->L + 16;
 }
 
 // samples per chunk of the state store, and the store's elements per sample
@@ -813,7 +868,7 @@ size_t eval_backward_staged_bytes(const tt_train* x, int64_t n) {
 
 template <typename T>
 bool eval_backward_staged_fits(const tt_train* x) {
-  return states_smem<T>(x) <= kStatesSmemMax;
+  return states_smem<T>(x, 64) <= kStatesSmemMax;
 }
 
 size_t eval_backward_workspace_bytes(const tt_train* x, int64_t n) {
@@ -861,15 +916,20 @@ int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, cons
   }
   if (zdim > 65535 || tiles > 65535) return fail(TT_ERR_UNSUPPORTED, "tt_eval_backward: train too large");
   TT_CUDA_CHECK(cudaMemsetAsync(acc, 0, (size_t)g * sizeof(double), s));
-  const size_t smem = states_smem<T>(x);
+  int S = states_samples<T>(x);
+  if (states_smem<T>(x, S) > kStatesSmemMax) S = 64;
+  const size_t smem = states_smem<T>(x, S);
   const int stage = states_stage_elems<T>(x);
   static int configured[2] = {-1, -1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   const int which = sizeof(T) == 8 ? 0 : 1;
   if (configured[which] != dev) {
-    TT_CUDA_CHECK(cudaFuncSetAttribute(eval_states_kernel<T, kStatesJB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kStatesSmemMax));
+    TT_CUDA_CHECK(cudaFuncSetAttribute(eval_states_kernel<T, kStatesJB, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStatesSmemMax));
+    if constexpr (sizeof(T) == 4)
+      TT_CUDA_CHECK(cudaFuncSetAttribute(eval_states_kernel<T, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kStatesSmemMax));
     configured[which] = dev;
   }
   // slices of at most 2048 samples (the FP32 sums of a slice stay short) and enough CTAs to fill the GPU
@@ -878,8 +938,17 @@ int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, cons
     const int64_t cn = std::min<int64_t>(C, n - c0);
     const uint8_t* dg = digits + c0 * L;
     const T* w = static_cast<const T*>(dvalues) + c0;
-    eval_states_kernel<T, kStatesJB><<<dim3((unsigned)ceil_div(cn, kStatesS), 2), kStatesS, smem, s>>>(
-        P, dg, cn, states, C, stage);
+    if constexpr (sizeof(T) == 4) {
+      if (states_one<T>(x))
+        eval_states_kernel<T, 64, true><<<dim3((unsigned)ceil_div(cn, S), 2), S, smem, s>>>(P, dg, cn, states, C,
+                                                                                          stage);
+      else
+        eval_states_kernel<T, kStatesJB, false><<<dim3((unsigned)ceil_div(cn, S), 2), S, smem, s>>>(
+            P, dg, cn, states, C, stage);
+    } else {
+      eval_states_kernel<T, kStatesJB, false><<<dim3((unsigned)ceil_div(cn, S), 2), S, smem, s>>>(P, dg, cn, states,
+                                                                                                  C, stage);
+    }
     TT_LAUNCH_CHECK();
     const int64_t slice = (std::min<int64_t>(slice_target, cn) + kAccK - 1) / kAccK * kAccK;
     const dim3 grid((unsigned)ceil_div(cn, slice), (unsigned)tiles, (unsigned)zdim);

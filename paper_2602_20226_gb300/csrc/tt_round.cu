@@ -288,6 +288,17 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
           // in FP64 and the truncation decision are FP64 (a one-sided Jacobi keeps each
           // column's rounding error relative to that column), and the kept left vectors
           // W_j / sigma_j are re-orthonormalised below.
+          if (tall && p >= kPrecondMin && B.tmp64) {
+            // the same preconditioning as the FP64 form, in FP64 on the FP64 copy of the
+            // factor: R2^T from the QR of R^T has R's singular values and left singular
+            // vectors, and the FP32 sweeps start from nearly orthogonal columns
+            TT_TRY(transpose_rm_to_cm<double>(s, B.sv.X, p, p, B.tmp64));
+            B.qr64.ldv = p;
+            B.qr64.status = B.qr.status;
+            TT_TRY(householder_qr<double>(s, B.tmp64, p, p, p, B.qr64));
+            TT_TRY(extract_rt<double>(s, B.tmp64, p, p, p, B.sv.X));
+            precond_flops = 4.0 * (double)p * p * p / 3.0;
+          }
           TT_TRY(convert_f64_to_f32(s, B.sv.X, (int64_t)p * p, B.X32));
           TT_TRY(jacobi_block_f32(s, B.sv, B.X32, p, p, p, nullptr, p, 30));
           TT_TRY(convert_f32_to_f64(s, B.X32, (int64_t)p * p, B.sv.X));
@@ -308,6 +319,14 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
             B.qr.ldv = p;
             TT_TRY(householder_qr<T>(s, B.tmp, p, p, p, B.qr));
             TT_TRY(extract_rt<T>(s, B.tmp, p, p, p, B.sv.X));
+            precond_flops = 4.0 * (double)p * p * p / 3.0;
+          } else if (tall && p >= kPrecondMin && B.tmp64) {
+            // the mixed form's factors beyond the FP32 kernel's size: the same, in FP64
+            TT_TRY(transpose_rm_to_cm<double>(s, B.sv.X, p, p, B.tmp64));
+            B.qr64.ldv = p;
+            B.qr64.status = B.qr.status;
+            TT_TRY(householder_qr<double>(s, B.tmp64, p, p, p, B.qr64));
+            TT_TRY(extract_rt<double>(s, B.tmp64, p, p, p, B.sv.X));
             precond_flops = 4.0 * (double)p * p * p / 3.0;
           }
           // one-sided Jacobi on the columns of the square factor X (p x p).  Pairs of columns

@@ -47,6 +47,9 @@ template <typename T>
 struct Bufs {
   T *A = nullptr, *Q = nullptr, *tmp = nullptr, *Rbuf = nullptr, *vsel = nullptr, *F = nullptr;
   float *X32 = nullptr, *G32 = nullptr;  // mixed-form bond SVD: FP32 factor, Newton-Schulz Gram
+  // mixed form: FP64 scratch of the preconditioning QR of the square factor
+  double* tmp64 = nullptr;
+  QrWork<double> qr64;
   // mixed form: W1 = V^T X and W2 = op(T) W1 of the batched driver's QR updates, in FP64
   double *w1d = nullptr, *w2d = nullptr;
   QrWork<T> qr;
@@ -74,6 +77,13 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B, bool batched = false)
   if (std::is_same<T, float>::value) {
     B.X32 = c.take<float>((size_t)D.r_max * D.r_max);
     B.G32 = c.take<float>((size_t)D.r_max * D.r_max);
+    if (!batched) {
+      B.tmp64 = c.take<double>((size_t)D.r_max * D.r_max);
+      B.qr64.nb = 16;
+      B.qr64.vbuf = c.take<double>((size_t)D.r_max * D.r_max);
+      B.qr64.tau = c.take<double>(D.r_max + 32);
+      B.qr64.tmat = c.take<double>((size_t)16 * 16 * (ceil_div(D.r_max, 16) + 1));
+    }
     if (batched) {
       B.w1d = c.take<double>((size_t)nb * D.r_max);
       B.w2d = c.take<double>((size_t)nb * D.r_max);
