@@ -502,6 +502,10 @@ int qr_panel_fast_batched(cudaStream_t s, int njobs, const PanelJob* d_jobs, int
   // cluster size per job: the smallest power of two whose row share fits shared memory
   int cs = 1;
   while (cs < kPanelCluster && panel_smem(nb, (mr_max + cs - 1) / cs) > kPanelSmemMax) cs *= 2;
+  // with few jobs, spread each job's rows over more SMs (a panel is bound by the FP64 pipe of
+  // the SMs that hold it): grow the cluster while all CTAs still fit one wave and every CTA
+  // keeps at least 64 rows
+  while (cs < kPanelCluster && (int64_t)njobs * cs * 2 <= num_sms() && mr_max / (cs * 2) >= 64) cs *= 2;
   const int chunk = (mr_max + cs - 1) / cs;
   const size_t smem = panel_smem(nb, chunk);
   if (smem > kPanelSmemMax) return fail(TT_ERR_UNSUPPORTED, "batched qr panel: too many rows");

@@ -343,8 +343,7 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         // (nearly dependent on others), which would also defeat the Newton-Schulz step
         TT_TRY(svd_truncate(s, B.sv, p, p, delta_scale, max_rank, mixed_svd ? kMixedSigmaFloor : 0.0));
         int rk[2] = {0, 0};
-        TT_TRY(read_back(s, B.sv.rank, &rk[0], sizeof(int)));
-        TT_TRY(read_back(s, B.sv.sweeps, &rk[1], sizeof(int)));
+        TT_TRY(read_back(s, B.sv.rank, &rk[0], 2 * sizeof(int)));  // rank, sweeps
         total_sweeps += rk[1];
         // executed work of the Jacobi: every sweep forms the three dot products of each of
         // the p (p - 1) / 2 pairs (6 p flops), and each rotation that was applied costs 6 p

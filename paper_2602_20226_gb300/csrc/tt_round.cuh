@@ -91,12 +91,12 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B, bool batched = false)
   }
   B.sv.sigma = c.take<double>(D.r_max);
   B.sv.perm = c.take<int>(D.r_max);
-  B.sv.rank = c.take<int>(1);
+  B.sv.rank = c.take<int>(2);
+  B.sv.sweeps = B.sv.rank + 1;  // next to the rank: one read-back per bond
   B.sv.bar = c.take<unsigned>(2);
   B.sv.rot = c.take<unsigned>(SvdWork::kMaxSweeps);
   B.sv.status = c.take<unsigned>(1);
   B.qr.status = B.sv.status;
-  B.sv.sweeps = c.take<int>(1);
   B.sv.norm = c.take<double>(1);
   B.sv.epoch = c.take<unsigned>((size_t)D.r_max + 2);
   return c.off + 256;

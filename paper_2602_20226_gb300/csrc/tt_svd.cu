@@ -840,12 +840,12 @@ __device__ __forceinline__ void rinv_colnorm_body(const double* R, int p, int ld
 constexpr int kRinvWarps = 4;
 
 template <int KS>
-__global__ void __launch_bounds__(32 * kRinvWarps) rinv_colnorm_cols_kernel(const double* __restrict__ R, int p,
-                                                                            int ldr, double* __restrict__ colsq) {
+__device__ __forceinline__ void rinv_colnorm_cols_body(const double* __restrict__ R, int p, int ldr,
+                                                       double* __restrict__ colsq, int bx) {
   extern __shared__ double rs[];  // rows [0, c0 + 32) x 32 columns (ld = rows), then 32 inverse diagonals
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = blockIdx.x * kRinvWarps + warp;
-  const int jmax = min(p - 1, blockIdx.x * kRinvWarps + kRinvWarps - 1);
+  const int j = bx * kRinvWarps + warp;
+  const int jmax = min(p - 1, bx * kRinvWarps + kRinvWarps - 1);
   double b[KS];
 #pragma unroll
   for (int q = 0; q < KS; ++q) b[q] = (32 * q + lane == j) ? 1.0 : 0.0;
@@ -875,6 +875,12 @@ __global__ void __launch_bounds__(32 * kRinvWarps) rinv_colnorm_cols_kernel(cons
     }
   }
   if (j < p && lane == 0) colsq[j] = nrm2;
+}
+
+template <int KS>
+__global__ void __launch_bounds__(32 * kRinvWarps) rinv_colnorm_cols_kernel(const double* __restrict__ R, int p,
+                                                                            int ldr, double* __restrict__ colsq) {
+  rinv_colnorm_cols_body<KS>(R, p, ldr, colsq, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) rinv_colnorm_kernel(const double* R, int p, int ldr,
@@ -923,6 +929,14 @@ __global__ void __launch_bounds__(256) rinv_colnorm_batched_kernel(const SvdJob*
   const SvdJob& J = jobs[blockIdx.y];
   if ((int)blockIdx.x * 8 >= J.n) return;
   rinv_colnorm_body(J.X, J.n, J.ldx, J.sigma, blockIdx.x);
+}
+
+// column-oriented form for the batch (bond ranks <= 32 KS): grid (ceil(n_max / 4), jobs)
+template <int KS>
+__global__ void __launch_bounds__(32 * kRinvWarps) rinv_colnorm_cols_batched_kernel(const SvdJob* __restrict__ jobs) {
+  const SvdJob& J = jobs[blockIdx.y];
+  if ((int)blockIdx.x * kRinvWarps >= J.n) return;  // the whole CTA leaves together
+  rinv_colnorm_cols_body<KS>(J.X, J.n, J.ldx, J.sigma, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(1024) certify_batched_kernel(const SvdJob* __restrict__ jobs, double unit,
@@ -1390,7 +1404,32 @@ int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, dou
                                        200 * 1024));
     configured = dev;
   }
-  rinv_colnorm_batched_kernel<<<dim3((unsigned)ceil_div(n_max, 8), (unsigned)nj), 256, smem, s>>>(d_jobs);
+  if (n_max <= 640) {
+    static int configured_cols = -1;
+    if (configured_cols != dev) {
+      TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_batched_kernel<4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_batched_kernel<8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_batched_kernel<16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_batched_kernel<20>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      configured_cols = dev;
+    }
+    const size_t smem_c = ((size_t)n_max * 32 + 32) * sizeof(double);
+    const dim3 grid((unsigned)ceil_div(n_max, kRinvWarps), (unsigned)nj);
+    if (n_max <= 128)
+      rinv_colnorm_cols_batched_kernel<4><<<grid, 32 * kRinvWarps, smem_c, s>>>(d_jobs);
+    else if (n_max <= 256)
+      rinv_colnorm_cols_batched_kernel<8><<<grid, 32 * kRinvWarps, smem_c, s>>>(d_jobs);
+    else if (n_max <= 512)
+      rinv_colnorm_cols_batched_kernel<16><<<grid, 32 * kRinvWarps, smem_c, s>>>(d_jobs);
+    else
+      rinv_colnorm_cols_batched_kernel<20><<<grid, 32 * kRinvWarps, smem_c, s>>>(d_jobs);
+  } else {
+    rinv_colnorm_batched_kernel<<<dim3((unsigned)ceil_div(n_max, 8), (unsigned)nj), 256, smem, s>>>(d_jobs);
+  }
   TT_LAUNCH_CHECK();
   certify_batched_kernel<<<nj, 1024, 0, s>>>(d_jobs, unit, rel_floor);
   TT_LAUNCH_CHECK();
