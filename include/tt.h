@@ -64,8 +64,10 @@ typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
  *                   cores in the sliced form of tt_gemm_f32_sliced (exact tensor-core sums)
  *                   where its tiles fill the GPU, compensated FP32 dot products below that;
  *                   a bond whose stored factor an FP64 certificate proves full rank skips
- *                   its SVD, the others get an FP32 one-sided Jacobi; singular values, the
- *                   truncation decision and the norm in FP64. */
+ *                   its SVD, the others get an FP64 preconditioning QR (of the factor's
+ *                   transpose) and an FP32 one-sided Jacobi (the FP64 one above the FP32
+ *                   kernel's shared-memory size); singular values, the truncation decision
+ *                   and the norm in FP64. */
 typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_prec;
 
 /* Limits of this build. */

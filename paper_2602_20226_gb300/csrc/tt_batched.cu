@@ -174,7 +174,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
   TT_TRY(lanes.init(s, streams, nstreams));
   constexpr bool kMixed = std::is_same<T, float>::value;
   const int prec = kMixed ? TT_PREC_MIXED : TT_PREC_FP64;
-  const int nb = panel_width<T>();
+  const int nb = panel_width<T>(true);
   const int64_t r_max = max_y_rank(n, W, x);
   const size_t a_bytes = arena_bytes(n, r_max, nb);
   // ---- workspace: [arena | results | train slices]
@@ -613,7 +613,7 @@ int batched_impl(int32_t n, const tt_mpo* W, const tt_train* x, tt_train* y, dou
 }  // namespace
 
 size_t batched_workspace_bytes(int32_t n, const tt_mpo* W, const tt_train* x, int32_t prec) {
-  const int nb = prec == TT_PREC_FP64 ? panel_width<double>() : panel_width<float>();
+  const int nb = prec == TT_PREC_FP64 ? panel_width<double>(true) : panel_width<float>(true);
   size_t b = arena_bytes(n, max_y_rank(n, W, x), nb) + results_bytes(n);
   for (int i = 0; i < n; ++i) b += train_slice_bytes(W[i], x[i], prec);
   return b;

@@ -119,10 +119,10 @@ size_t round_workspace_bytes(const tt_train* x, int prec, bool batched) {
   Carver c(nullptr);
   if (prec == TT_PREC_FP64) {
     Bufs<double> B;
-    return carve(c, D, panel_width<double>(), B, batched);
+    return carve(c, D, panel_width<double>(batched), B, batched);
   }
   Bufs<float> B;
-  return carve(c, D, panel_width<float>(), B, batched);
+  return carve(c, D, panel_width<float>(batched), B, batched);
 }
 
 size_t round_record_bytes(const tt_train* x) {

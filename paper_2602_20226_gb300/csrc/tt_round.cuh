@@ -102,9 +102,13 @@ size_t carve(Carver& c, const Dims& D, int nb, Bufs<T>& B, bool batched = false)
   return c.off + 256;
 }
 
+// Householder panel width: 16 columns, except the batched driver's mixed form (32: its QR
+// updates run as dense batched GEMMs over all jobs, and the wider panels carry its largest
+// trains' error further below 1e-6); the single-train mixed form takes 16, whose panels cost
+// about half per column (emulated error on the 2D rank-64 train 5.0e-7 -> 5.5e-7)
 template <typename T>
-inline int panel_width() {
-  return sizeof(T) == 8 ? 16 : 32;
+inline int panel_width(bool batched = false) {
+  return sizeof(T) == 8 ? 16 : (batched ? 32 : 16);
 }
 
 // Relative resolution of the mixed form's bond SVD (see the truncation call).

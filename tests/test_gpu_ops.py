@@ -106,7 +106,7 @@ def test_inner_parity(cuda_lib, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("case", [(10, 8, 2, 1000), (40, 64, 2, 5000), (6, 130, 3, 777), (3, 2, 5, 0)])
+@pytest.mark.parametrize("case", [(10, 8, 2, 1000), (40, 64, 2, 5000), (7, 37, 3, 2000), (6, 130, 3, 777), (3, 2, 5, 0)])
 def test_eval_parity(cuda_lib, dtype, case):
     tt = cuda_lib
     L, r, d, n = case
