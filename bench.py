@@ -243,6 +243,7 @@ def run_ours(args):
         extra["batched"] = bench_batched(tt, dev, Wm, n_tt=args.batch_trains, rank=rank, world=world)
         extra["eval"] = bench_eval(tt, dev)
         extra["small_1d"] = bench_small(tt, dev)
+        extra["grouped_2d"] = bench_grouped(tt, dev)
         extra["laplacian3d_rank256"] = bench_large(tt, dev, "laplacian3d")
         if args.large:
             extra["hadamard_square_rank64"] = bench_large(tt, dev, "hadamard")
@@ -450,6 +451,34 @@ def bench_eval(tt, dev, n=1 << 20, L=40, r=64):
                          "flops": "3x the forward: prefix sweep, suffix sweep, per-site sums",
                          "what": "tt_eval_backward (gradient w.r.t. the cores): FP32 prefix/suffix states "
                                  "and per-site sums over 2048-sample slices, FP64 across slices"}}
+
+
+def bench_grouped(tt, dev, reps=3):
+    """The 2D workload in the grouped-digit layout: the digits (x_q, y_q) of each scale on one
+    core of mode 4 (L = 20, rank 64, FP64), the grouped Laplacian MPO (rank 5), apply + round
+    at 1e-8; median of three calls after one warm-up, host-timed with device syncs."""
+    import torch
+
+    from paper_2602_20226_gb300 import inputs, qtt
+    from paper_2602_20226_gb300.flops import apply_flops, round_flops
+
+    X = tt.TT.from_numpy(inputs.random_tt(2, 20, 4, 64), device=dev)
+    W = tt.MPO.from_numpy(qtt.group_mpo_sites(qtt.laplacian_mpo(2, 20), 2), device=dev)
+    ts = []
+    for i in range(reps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Y = tt.tt_apply_mpo(W, X)
+        Z, _ = tt.tt_round(Y, 1e-8)
+        torch.cuda.synchronize(dev)
+        if i:
+            ts.append(time.perf_counter() - t0)
+    sec = float(np.median(ts))
+    fl = apply_flops([int(v) for v in W.ranks], X.ranks, X.dims) + round_flops(Y.ranks, Z.ranks, X.dims)["total"]
+    return {"workload": "2D quantics TT, grouped digits (x_q, y_q) per core: L=20, d=4, rank 64, FP64, "
+                        "grouped Laplacian MPO rank 5, apply + tt_round eps=1e-8 (median of 3 host-timed calls)",
+            "ms": round(sec * 1e3, 3), "value": round(fl / sec / 1e9, 2), "unit": "GFLOP/s",
+            "ranks_in_max": max(Y.ranks), "ranks_out_max": max(Z.ranks)}
 
 
 def bench_large(tt, dev, case):

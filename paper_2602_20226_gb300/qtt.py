@@ -12,7 +12,7 @@ import math
 import numpy as np
 
 __all__ = ["laplacian_mpo", "second_difference_mpo", "exp_tt", "cos_tt", "sin_tt",
-           "interleave_sites"]
+           "interleave_sites", "group_sites", "group_mpo_sites"]
 
 _I = np.eye(2)
 _J = np.array([[0.0, 0.0], [1.0, 0.0]])  # shift by +1 within one binary digit: J[1][0] = 1
@@ -129,3 +129,39 @@ def cos_tt(bits: int, lower: float, upper: float, v: float, x0: float = 0.0,
 def sin_tt(bits: int, lower: float, upper: float, v: float, x0: float = 0.0) -> list[np.ndarray]:
     """sin(v (x - x0)) as the rotation TT shifted by pi/2."""
     return cos_tt(bits, lower, upper, v, x0, phase=-0.5 * math.pi)
+
+
+def group_sites(cores: list[np.ndarray], g: int) -> list[np.ndarray]:
+    """The same tensor with every g consecutive sites merged into one core of mode d^g: the
+    grouped ("interleaved") layout that puts the digits (x_q, y_q[, z_q]) of one scale on a
+    single core (Section 6, TrainShape mode 'interleaved'; d = 4 in 2D, 8 in 3D).  The
+    merged index keeps the first site's digit most significant, i = i_1 d_2 + i_2, as the
+    quantics order of Eq. (quantization).  len(cores) must be a multiple of g."""
+    if g < 1 or len(cores) % g:
+        raise ValueError("the number of sites must be a multiple of the group size")
+    out = []
+    for k in range(0, len(cores), g):
+        c = cores[k]
+        for nxt in cores[k + 1:k + g]:
+            r0, d1, _ = c.shape
+            _, d2, r2 = nxt.shape
+            c = np.tensordot(c, nxt, axes=([2], [0])).reshape(r0, d1 * d2, r2)
+        out.append(np.ascontiguousarray(c))
+    return out
+
+
+def group_mpo_sites(cores: list[np.ndarray], g: int) -> list[np.ndarray]:
+    """group_sites for an MPO: cores W[a, i, j, a'] merged g at a time into
+    W[a, (i_1 .. i_g), (j_1 .. j_g), a'] (output and input digits each first-site major)."""
+    if g < 1 or len(cores) % g:
+        raise ValueError("the number of sites must be a multiple of the group size")
+    out = []
+    for k in range(0, len(cores), g):
+        c = cores[k]
+        for nxt in cores[k + 1:k + g]:
+            a0, do1, di1, _ = c.shape
+            _, do2, di2, a2 = nxt.shape
+            t = np.tensordot(c, nxt, axes=([3], [0]))  # a0, do1, di1, do2, di2, a2
+            c = t.transpose(0, 1, 3, 2, 4, 5).reshape(a0, do1 * do2, di1 * di2, a2)
+        out.append(np.ascontiguousarray(c))
+    return out
