@@ -346,10 +346,9 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
         TT_TRY(read_back(s, B.sv.rank, &rk[0], 2 * sizeof(int)));  // rank, sweeps
         total_sweeps += rk[1];
         // executed work of the Jacobi: every sweep forms the three dot products of each of
-        // the p (p - 1) / 2 pairs (6 p flops) - the four-warp kernel (64 < p <= 512) only those of
-        // round 0's p / 2 pairs and gamma alone (2 p) for the rest, carrying the column norms -
-        // and each rotation that was applied costs 6 p more (the kernels count them per sweep);
-        // the mixed form's FP32 sweeps are bounded by 12 p flops per pair
+        // the p (p - 1) / 2 pairs (6 p flops), and each rotation that was applied costs 6 p
+        // more (the kernels count them per sweep); the mixed form's FP32 sweeps are bounded
+        // by 12 p flops per pair
         if (prof.on) {
           double ex = precond_flops;
           const double pairs = 0.5 * (double)p * (p - 1);
@@ -362,9 +361,7 @@ int round_impl(const tt_train* x, double eps, int64_t max_rank, tt_train* out, d
             if (sw > 0) TT_TRY(read_back(s, B.sv.rot, rots.data(), sw * sizeof(unsigned)));
             double nrot = 0.0;
             for (int q = 0; q < sw; ++q) nrot += rots[q];
-            const bool wpp = p > 64 && p <= 512;  // the norm-carrying four-warp kernel
-            const double dots = wpp ? 6.0 * p * (0.5 * p) + 2.0 * p * (pairs - 0.5 * p) : 6.0 * p * pairs;
-            ex += dots * sw + 6.0 * p * nrot;
+            ex += 6.0 * p * (pairs * sw + nrot);
           }
           prof.set_executed(pe_jacobi, ex);
         }

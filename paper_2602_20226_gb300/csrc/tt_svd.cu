@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(double* X, int nrow, int nco
 // first scaled by a power of two (exact), so d^2 + 4 ga^2 can neither overflow nor underflow,
 // and the acceptance test |ga| > tol sqrt(al be) is taken as ga^2 > tol^2 al be on them.
 __device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga, double tol, double negl, double& c,
-                                                double& sn, double* t_out = nullptr) {
+                                                double& sn) {
   if ((al < negl && be < negl) || ga == 0.0) return false;
   const int e = ilogb(fmax(al, be));
   al = scalbn(al, -e);
@@ -224,7 +224,6 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga,
   const double t = copysign(1.0, d) * (2.0 * ga) / (fabs(d) + h);
   c = rsqrt(fma(t, t, 1.0));
   sn = c * t;
-  if (t_out) *t_out = t;
   return sn != 0.0;
 }
 
@@ -370,14 +369,11 @@ __global__ void __launch_bounds__(256) jacobi_small_kernel(double* X, int nrow, 
 // warp sums take 6 additions per lane (warp_sum3_split); register chunks wholly beyond a
 // warp's rows are skipped by a warp-uniform test instead of being issued with every lane
 // predicated off.  Dataflow ordering between pairs as in jacobi_kernel.
-// Squared column norms are carried in cn between the rounds (a rotation by tan(theta) = t maps
-// (alpha, beta) to (alpha - t gamma, beta + t gamma)) and recomputed from the columns in round
-// 0 of every sweep, so the other rounds form only gamma: one FMA per row instead of three.
 template <int WPP, int TPL>
 __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nrow, int ncol, int ldx, double tol,
                                                              double negl_scale, const double* norm, int max_sweeps,
                                                              unsigned* bar, unsigned* rot, unsigned* status,
-                                                             int* sweeps_out, unsigned* epoch, double* cn) {
+                                                             int* sweeps_out, unsigned* epoch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double nl = negl_scale > 0.0 ? negl_scale * __ldcg(norm) : 0.0;
   const double negl = nl * nl;
@@ -417,8 +413,7 @@ __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nro
         }
         double* xa = X + (int64_t)a * ldx;
         double* xb = X + (int64_t)b * ldx;
-        const bool full = rnd == 0;  // every column takes part in round 0 once
-        if (real_b || full) {  // the padding partner of round 0: column a's norm alone
+        if (real_b) {
           double ra[TPL], rb[TPL];
           double al = 0.0, be = 0.0, ga = 0.0;
 #pragma unroll
@@ -428,52 +423,31 @@ __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nro
               const int i = i_lo + lane + 32 * u;
               if (i < i_hi) {
                 ra[u] = __ldcg(xa + i);
-                if (real_b) rb[u] = __ldcg(xb + i);
+                rb[u] = __ldcg(xb + i);
               }
             }
           }
-          if (full) {
 #pragma unroll
-            for (int u = 0; u < TPL; ++u) {
-              if (i_lo + 32 * u < i_hi) {
-                al = fma(ra[u], ra[u], al);
-                be = fma(rb[u], rb[u], be);
-                ga = fma(ra[u], rb[u], ga);
-              }
+          for (int u = 0; u < TPL; ++u) {
+            if (i_lo + 32 * u < i_hi) {
+              al = fma(ra[u], ra[u], al);
+              be = fma(rb[u], rb[u], be);
+              ga = fma(ra[u], rb[u], ga);
             }
-            const double v = warp_sum3_split(al, be, ga, lane);
-            if ((lane & 7) == 0 && lane < 24) red[warp][lane >> 3] = v;
-          } else {
-#pragma unroll
-            for (int u = 0; u < TPL; ++u)
-              if (i_lo + 32 * u < i_hi) ga = fma(ra[u], rb[u], ga);
-            ga = warp_sum(ga);
-            if (lane == 0) red[warp][2] = ga;
           }
+          const double v = warp_sum3_split(al, be, ga, lane);
+          if ((lane & 7) == 0 && lane < 24) red[warp][lane >> 3] = v;
           __syncthreads();
           if (threadIdx.x == 0) {
-            ga = 0.0;
+            al = be = ga = 0.0;
 #pragma unroll
-            for (int w = 0; w < WPP; ++w) ga += red[w][2];
-            if (full) {
-              al = be = 0.0;
-#pragma unroll
-              for (int w = 0; w < WPP; ++w) {
-                al += red[w][0];
-                be += red[w][1];
-              }
-            } else {
-              al = __ldcg(cn + a);
-              be = __ldcg(cn + b);
+            for (int w = 0; w < WPP; ++w) {
+              al += red[w][0];
+              be += red[w][1];
+              ga += red[w][2];
             }
-            double c = 1.0, sn = 0.0, tn = 0.0;
-            const bool doit = real_b && jacobi_rotation(al, be, ga, tol, negl, c, sn, &tn);
-            if (doit) {
-              al = fma(-tn, ga, al);
-              be = fma(tn, ga, be);
-            }
-            __stcg(cn + a, al);
-            if (real_b) __stcg(cn + b, be);
+            double c = 1.0, sn = 0.0;
+            const bool doit = jacobi_rotation(al, be, ga, tol, negl, c, sn);
             s_cs[0] = c;
             s_cs[1] = sn;
             s_doit = doit;
@@ -1199,8 +1173,7 @@ int launch_wpp(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, doubl
   const double* nrm = w.norm;
   unsigned *bar = w.bar, *rot = w.rot, *st = w.status, *ep = w.epoch;
   int* sw = w.sweeps;
-  double* cn = w.sigma;  // free until svd_truncate forms the singular values
-  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &negl_scale, &nrm, &max_sweeps, &bar, &rot, &st, &sw, &ep, &cn};
+  void* args[] = {&X, &nrow, &ncol, &ldx, &tol, &negl_scale, &nrm, &max_sweeps, &bar, &rot, &st, &sw, &ep};
   TT_CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_wpp_kernel<WPP, TPL>, dim3(blocks), dim3(NT), args,
                                             0, s));
   note_launch();
