@@ -489,9 +489,10 @@ __global__ void __launch_bounds__(32 * WPP) jacobi_wpp_kernel(double* X, int nro
 
 // FP32 one-sided Jacobi with accumulated rotations, organised as a block round-robin:
 // the columns are cut into groups of 16; in each outer round a CTA takes one pair of
-// groups (32 columns of X and of V) into shared memory and sweeps all pairs among
-// them (31 inner rounds of 16 rotations, one warp per pair, __syncthreads between
-// inner rounds), then writes them back.  Group pairs follow the round-robin order,
+// groups (32 columns of X and of V) into shared memory and rotates the 256 pairs across
+// the two groups (16 inner rounds of 16 rotations, one warp per pair, __syncthreads between
+// inner rounds; in a sweep's first outer round also the pairs inside each group), then
+// writes them back.  Group pairs follow the round-robin order,
 // so a grid barrier is needed only between outer rounds: 2G - 1 per sweep for G
 // groups instead of p - 1.  The mixed form uses it as the fast part of its bond SVD.
 // Global -> shared copy of the C2 columns listed in cols (n values each, column c of
@@ -655,17 +656,35 @@ __global__ void __launch_bounds__(32 * GS) jacobi_block_f32_kernel(float* X, int
         load_cols<8>(Xs, X, cols, C2, nrow, ldx);
         if (V) load_cols<8>(Vs, V, cols, C2, ncol, ldv);
         __syncthreads();
-        // inner round-robin over the 2 GS local slots: 2 GS - 1 rounds x GS pairs
+        // Each pair of columns once per sweep: the pairs inside each group in the sweep's first
+        // outer round (every group takes part in it once; the two groups' round-robins side by
+        // side, GS - 1 rounds of GS / 2 + GS / 2 pairs), and the GS x GS pairs across the two
+        // groups in every outer round (GS rounds of GS disjoint pairs, slot w of the first group
+        // with slot (w + ir) mod GS of the second)
         unsigned local = 0;
-        for (int ir = 0; ir < C2 - 1; ++ir) {
-          int a, b;
-          if (warp == 0) {
-            a = ir;
-            b = C2 - 1;
-          } else {
-            a = (ir + warp) % (C2 - 1);
-            b = (ir - warp + C2 - 1) % (C2 - 1);
+        if (r == 0) {
+          constexpr int H = kJbGroup / 2;
+          const int wg = warp % H, base = warp < H ? 0 : kJbGroup;
+          for (int ir = 0; ir < kJbGroup - 1; ++ir) {
+            int a, b;
+            if (wg == 0) {
+              a = ir;
+              b = kJbGroup - 1;
+            } else {
+              a = (ir + wg) % (kJbGroup - 1);
+              b = (ir - wg + kJbGroup - 1) % (kJbGroup - 1);
+            }
+            a += base;
+            b += base;
+            if (cols[a] >= 0 && cols[b] >= 0 &&
+                rotate_pair_f32<TPL>(Xs + (size_t)a * nrow, Xs + (size_t)b * nrow, Vs + (size_t)a * ncol,
+                                     Vs + (size_t)b * ncol, nrow, V ? ncol : 0, lane, tol, negl))
+              ++local;
+            __syncthreads();
           }
+        }
+        for (int ir = 0; ir < kJbGroup; ++ir) {
+          const int a = warp, b = kJbGroup + (warp + ir) % kJbGroup;
           if (cols[a] >= 0 && cols[b] >= 0 &&
               rotate_pair_f32<TPL>(Xs + (size_t)a * nrow, Xs + (size_t)b * nrow, Vs + (size_t)a * ncol,
                                    Vs + (size_t)b * ncol, nrow, V ? ncol : 0, lane, tol, negl))
