@@ -332,11 +332,10 @@ int panel_dispatch(cudaStream_t s, TIO* A, int lda, int m, int j0, int jb, TIO* 
 
 // ------------------------------------------------------------------ block reflector
 constexpr int RT = 256;   // threads
-constexpr int RNC = 2;    // columns of X per CTA
 constexpr int RCH = 128;  // rows of V staged per chunk
 
-// X[:, c0 .. c0 + RNC) <- (I - V op(T) V^T) X[:, ...]
-template <typename T, int NB>
+// X[:, c0 .. c0 + RNC) <- (I - V op(T) V^T) X[:, ...]; RNC columns of X per CTA
+template <typename T, int NB, int RNC>
 __device__ __forceinline__ void reflector_body(const T* __restrict__ V, int ldv, int mr, int jb,
                                                const double* __restrict__ Tm, int ldt, bool transpose_t,
                                                T* __restrict__ X, int ldx, int nc, int c0) {
@@ -467,10 +466,10 @@ __device__ __forceinline__ void reflector_body(const T* __restrict__ V, int ldv,
   }
 }
 
-template <typename T, int NB>
+template <typename T, int NB, int RNC>
 __global__ void __launch_bounds__(RT) reflector_kernel(const T* V, int ldv, int mr, int jb, const double* Tm, int ldt,
                                                        bool transpose_t, T* X, int ldx, int nc) {
-  reflector_body<T, NB>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc, blockIdx.x * RNC);
+  reflector_body<T, NB, RNC>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc, blockIdx.x * RNC);
 }
 
 }  // namespace
@@ -488,10 +487,19 @@ template <typename T>
 int apply_block_reflector(cudaStream_t s, const T* V, int ldv, int mr, int jb, const double* Tm, int ldt,
                           bool transpose_t, T* X, int ldx, int nc) {
   if (nc <= 0 || mr <= 0 || jb <= 0) return TT_OK;
-  const unsigned grid = (unsigned)ceil_div(nc, RNC);
-  if (jb <= 16) reflector_kernel<T, 16><<<grid, RT, 0, s>>>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc);
-  else if (jb <= 32) reflector_kernel<T, 32><<<grid, RT, 0, s>>>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc);
-  else return fail(TT_ERR_UNSUPPORTED, "block reflector: width above 32");
+  // two columns of X per CTA, or one when that still leaves SMs idle (a CTA's time is its
+  // columns' 4 mr jb multiply-adds on one SM's FP64 pipe)
+  const bool one = nc <= num_sms();
+  const unsigned grid = (unsigned)ceil_div(nc, one ? 1 : 2);
+  if (jb <= 16) {
+    if (one) reflector_kernel<T, 16, 1><<<grid, RT, 0, s>>>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc);
+    else reflector_kernel<T, 16, 2><<<grid, RT, 0, s>>>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc);
+  } else if (jb <= 32) {
+    if (one) reflector_kernel<T, 32, 1><<<grid, RT, 0, s>>>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc);
+    else reflector_kernel<T, 32, 2><<<grid, RT, 0, s>>>(V, ldv, mr, jb, Tm, ldt, transpose_t, X, ldx, nc);
+  } else {
+    return fail(TT_ERR_UNSUPPORTED, "block reflector: width above 32");
+  }
   TT_LAUNCH_CHECK();
   return TT_OK;
 }
