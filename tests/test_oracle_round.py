@@ -75,6 +75,61 @@ def test_round_two_sites_is_truncated_svd():
         assert abs(err - (tails[r_want] if r_want < 16 else 0.0)) <= 1e-12 * nrm
 
 
+def _orthogonal_terms_tt(s, L, d, seed):
+    """x = sum_j s_j a_j^(1) (x) ... (x) a_j^(L), the a_j^(k) orthonormal over j at every site.
+
+    Every unfolding of x is then sum_j s_j (left_j)(right_j)^T with orthonormal left and right
+    factors, so its singular values are exactly s, at every bond."""
+    m = len(s)
+    g = np.random.default_rng(seed)
+    vecs = [np.linalg.qr(g.standard_normal((d, m)))[0] for _ in range(L)]  # d x m, orthonormal columns
+    cores = [np.einsum("ij,j->ij", vecs[0], s).reshape(1, d, m)]
+    for k in range(1, L - 1):
+        c = np.zeros((m, d, m))
+        for j in range(m):
+            c[j, :, j] = vecs[k][:, j]
+        cores.append(c)
+    cores.append(vecs[L - 1].T.reshape(m, d, 1))
+    # an invertible gauge G_k at every bond (core k <- core k G_k, core k+1 <- G_k^-1 core k+1):
+    # the tensor is unchanged, but the cores are no longer orthogonal and the first one carries
+    # 3 ||x|| (G_1 = 3 x an orthogonal matrix)
+    for k in range(L - 1):
+        if k == 0:
+            gk = 3.0 * np.linalg.qr(g.standard_normal((m, m)))[0]
+        else:
+            gk = np.eye(m) + 0.3 * g.standard_normal((m, m))
+        cores[k] = np.einsum("adb,bc->adc", cores[k], gk)
+        cores[k + 1] = np.einsum("ab,bdc->adc", np.linalg.inv(gk), cores[k + 1])
+    return cores
+
+
+@pytest.mark.parametrize("L", [3, 5, 9])
+def test_round_known_bond_spectrum(L):
+    """Bond spectrum s at every bond (above): round_tt keeps, at every bond, the smallest r'
+    whose tail (sum_{j >= r'} s_j^2)^(1/2) is <= delta = eps ||x|| / sqrt(L - 1), and its error is
+    exactly that tail (the dropped terms are orthogonal to the kept ones).  eps is set so that
+    delta sits at 0.7x and 1.4x of each tail, so a threshold off by sqrt(L - 1) >= 2 (L >= 5), a
+    norm read off the gauged input instead of the orthogonalised first core (3x), or a misplaced
+    tail moves the rank."""
+    s = np.array([1.0, 0.5, 0.1, 0.02])
+    x = _orthogonal_terms_tt(s, L, 5, seed=40 + L)
+    fx = core.full(x)
+    nrm = float(np.linalg.norm(s))
+    assert abs(np.linalg.norm(fx) - nrm) <= 1e-13
+    assert abs(np.linalg.norm(x[0]) - 3.0 * nrm) <= 1e-13  # the input's first core is not the norm
+    tails = [float(np.sqrt(np.sum(s[j:] ** 2))) for j in range(len(s) + 1)]  # tails[4] = 0
+    for t in (1, 2, 3):
+        for factor in (0.7, 1.4):
+            delta = factor * tails[t]
+            eps = delta * math.sqrt(L - 1) / nrm
+            y = core.round_tt(x, eps)
+            r_want = min(j for j in range(1, len(s) + 1) if tails[j] <= delta)
+            assert r_want == (t if factor > 1 else t + 1)
+            assert core.ranks(y) == [1] + [r_want] * (L - 1) + [1], (t, factor)
+            err = np.linalg.norm(core.full(y) - fx)
+            assert abs(err - tails[r_want]) <= 1e-13, (t, factor, err)
+
+
 def test_round_max_rank_cap():
     x = _tt(8, 10, 6)
     y = core.round_tt(x, 1e-14, max_rank=3)
