@@ -11,9 +11,11 @@ Modules
               rounding, gauge-invariant error e(a, b)            (Sections 2, 3.1, 3.2)
   structured  closed-form exp / cos / sin / polynomial TTs, shift MPOs and
               Dirichlet Laplacians                              (Section 4)
-  grad        hand-derived adjoints of apply / hadamard / inner / evaluate
+  grad        hand-derived adjoints of apply / hadamard / inner / evaluate / rounding
+  qft         the Fourier (DFT) matrix as a tensor train from element-wise products of
+              rank-b_q factors, rounded at a maximum rank            (Section 4.3)
 
 Every function is pinned by ``tests/test_oracle_*.py`` against brute force on
 full tensors, closed forms, invariants or finite differences.
 """
-from . import core, grad, structured  # noqa: F401
+from . import core, grad, qft, structured  # noqa: F401

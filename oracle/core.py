@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module; only the
 tests, the smoke check and the CPU-baseline leg of the benchmark may call it.
 It shares no code with the CUDA path.
 
-Plain numpy in float64.  A library primitive (matmul/einsum, Householder QR via
+Plain numpy in float64 (complex128 where the cores are complex: the rounding of the Fourier
+TT of Section 4.3).  A library primitive (matmul/einsum, Householder QR via
 LAPACK geqrf/orgqr, SVD via LAPACK) serves as a single step; no blocking, fusion
 or reordering is added beyond the definitions below.
 
@@ -177,7 +178,9 @@ def orthogonalize_rl(x):
     transpose), C_k <- Q (orthonormal rows), C_{k-1} <- C_{k-1} L.
     Afterwards ||x|| = ||C_1||_F.
     """
-    c = [np.array(g, dtype=np.float64, copy=True) for g in x]
+    # float64, or complex128 for complex cores (the Fourier TT of Section 4.3); with complex
+    # cores q^T still has orthonormal rows, so the same steps hold
+    c = [np.array(g, dtype=np.result_type(g, np.float64), copy=True) for g in x]
     for k in range(len(c) - 1, 0, -1):
         r0, d, r1 = c[k].shape
         m = c[k].reshape(r0, d * r1)

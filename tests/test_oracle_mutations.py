@@ -18,10 +18,11 @@ import textwrap
 
 import pytest
 
-from oracle import core, grad, structured
+from oracle import core, grad, qft, structured
 
 import test_oracle_exact as pe
 import test_oracle_grad as pg
+import test_oracle_qft as pq
 import test_oracle_round as pr
 import test_oracle_structured as ps
 
@@ -129,6 +130,19 @@ CASES = [
     ("laplacian_mpo: pending terms of other dimensions dropped", structured, "laplacian_mpo",
      "if pending_other:", "if False:",
      [lambda: ps.test_laplacian_dense(2, 4, 5)]),
+    # ---- the Fourier tensor train (Section 4.3)
+    ("fourier factors: column digits not reversed", qft, "_weights",
+     "w = [int(np.prod(bases[:p], dtype=np.int64)) for p in range(n)]", "w = list(c)",
+     [lambda: pq.test_exact_product_is_the_fft([3, 2, 2, 5, 2, 2])]),
+    ("fourier factor: delta(s, i_q) dropped", qft, "factor_mpo",
+     "g[s, s, jp, s] = phase", "g[s, :, jp, s] = phase",
+     [lambda: pq.test_factor_mpos_are_rank_bq_phases([3, 2, 2, 5, 2, 2])]),
+    ("fourier factor: exponent without the row weight c_q", qft, "factor_mpo",
+     "(s * c[q] * w[p] * jp) % N", "(s * w[p] * jp) % N",
+     [lambda: pq.test_factor_mpos_are_rank_bq_phases([3, 2, 2, 5, 2, 2])]),
+    ("dft matrix: v = exp(+2 pi i / N)", qft, "dft_rows",
+     "table = np.exp(-2j * np.pi", "table = np.exp(2j * np.pi",
+     [pq.test_paper_distances_n8192]),
     # ---- adjoints (Section 3.3 environments; the reverse of the rounding sweeps)
     ("apply_mpo_vjp: dW with i and j swapped", grad, "apply_mpo_vjp",
      '"rjs,aribs->aijb"', '"rjs,aribs->ajib"',
