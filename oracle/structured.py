@@ -13,8 +13,6 @@ import math
 
 import numpy as np
 
-from . import core
-
 
 def coefficients(bases):
     """c_q = prod_{r > q} b_r (Section 2, Eq. (quantization))."""

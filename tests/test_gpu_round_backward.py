@@ -17,7 +17,6 @@ entry as the floor.
 """
 import numpy as np
 import pytest
-import torch
 
 from oracle import core, grad
 from paper_2602_20226_gb300 import _abi, inputs
