@@ -29,6 +29,11 @@
  * Errors: every call returns a tt_status.  Arguments are validated on the host
  * before anything is enqueued; on a validation error nothing is launched.
  * tt_last_error() returns a message for the last failing call of this thread.
+ *
+ * Threads: calls may come from several host threads at once, on any devices, as long as
+ * they use different workspaces (and tt_inner_noalloc, whose scratch is shared, is not
+ * overlapped).  The per-device launch settings the library caches on first use (SM count,
+ * occupancy, shared-memory opt-ins) are kept in atomics.
  */
 #ifndef LIBTT_TT_H
 #define LIBTT_TT_H

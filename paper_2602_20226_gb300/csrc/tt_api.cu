@@ -49,14 +49,19 @@ int fail(int code, const std::string& msg) {
 }
 
 int num_sms() {
-  static int dev_cached = -1, sms = 0;
+  // cached for the last device asked about; the count is stored before the device tag, so a
+  // thread that sees the tag sees its count
+  static std::atomic<int> dev_cached{-1}, sms{0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-  if (dev != dev_cached) {
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
-    dev_cached = dev;
+  if (dev != dev_cached.load()) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    sms.store(v);
+    dev_cached.store(dev);
+    return v;
   }
-  return sms;
+  return sms.load();
 }
 
 namespace {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <vector>
 #include <stdint.h>

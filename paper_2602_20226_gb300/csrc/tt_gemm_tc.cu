@@ -315,7 +315,7 @@ constexpr size_t tc_smem_bytes() {
 
 template <int BN, typename Acc>
 int launch_tc(cudaStream_t s, const TcArgs& a) {
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - NST)
 
 template <int NST, typename K>
 int sliced_configure(K kernel) {
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {

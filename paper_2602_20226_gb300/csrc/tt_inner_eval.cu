@@ -673,7 +673,7 @@ int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values,
     int stage = 1;
     for (int k = 0; k < x->L; ++k)
       stage = std::max(stage, P.r[k] * P.d[k] * eval_row_pad<T>(P.r[k + 1]));
-    static int configured_s[2] = {-1, -1};
+    static std::atomic<int> configured_s[2] = {{-1}, {-1}};
     int dev = 0;
     TT_CUDA_CHECK(cudaGetDevice(&dev));
     const int which = sizeof(T) == 8 ? 0 : 1;
@@ -717,7 +717,7 @@ int eval_impl(const tt_train* x, const uint8_t* digits, int64_t n, void* values,
   auto smem_for = [&](int SS) { return 2 * (size_t)P.rmax * SS * sizeof(T); };
   while (S > 32 && smem_for(S) > 200 * 1024) S /= 2;
   if (smem_for(S) > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "tt_eval: rank too large");
-  static int configured[2] = {-1, -1};
+  static std::atomic<int> configured[2] = {{-1}, {-1}};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   const int which = sizeof(T) == 8 ? 0 : 1;
@@ -920,7 +920,7 @@ int eval_backward_impl(const tt_train* x, const uint8_t* digits, int64_t n, cons
   if (states_smem<T>(x, S) > kStatesSmemMax) S = 64;
   const size_t smem = states_smem<T>(x, S);
   const int stage = states_stage_elems<T>(x);
-  static int configured[2] = {-1, -1};
+  static std::atomic<int> configured[2] = {{-1}, {-1}};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   const int which = sizeof(T) == 8 ? 0 : 1;

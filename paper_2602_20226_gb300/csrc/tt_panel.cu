@@ -292,7 +292,7 @@ int allow_smem(K kernel, size_t bytes) {
 template <typename TIO, int NB, int CS>
 int launch_panel(cudaStream_t s, TIO* A, int lda, int m, int j0, int jb, TIO* tau, double* Tm, int ldt, TIO* Vb,
                  int ldv, int chunk) {
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {

@@ -149,7 +149,7 @@ int trsm_rt(cudaStream_t s, double* X, int rows, int n, int64_t sxr, int64_t sxc
   TT_LAUNCH_CHECK();
   const size_t smem = (size_t)kTrsmWarps * n * sizeof(double);
   if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "tt_round_backward: factor too large for the solve");
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {

@@ -1174,7 +1174,7 @@ __global__ void svd_left_batched_kernel(const SvdJob* __restrict__ jobs) {
 template <int TPL>
 int launch_wpp(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, double negl_scale, int max_sweeps) {
   constexpr int WPP = 4, NT = 32 * WPP;
-  static int cfg_dev = -1, cfg_blocks = 0;
+  static std::atomic<int> cfg_dev{-1}, cfg_blocks{0};  // blocks stored before the device tag
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (cfg_dev != dev) {
@@ -1184,7 +1184,7 @@ int launch_wpp(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, doubl
     cfg_dev = dev;
   }
   const int npairs = (ncol + 1) / 2;
-  int blocks = std::min(npairs, cfg_blocks);
+  int blocks = std::min(npairs, cfg_blocks.load());
   if (blocks < 1) blocks = 1;
   TT_CUDA_CHECK(cudaMemsetAsync(w.epoch, 0, (size_t)ncol * sizeof(unsigned), s));
   double* X = w.X;
@@ -1229,7 +1229,7 @@ int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, do
   if (w.epoch != nullptr && nrow <= 512) return launch_jacobi_wpp(s, w, nrow, ncol, tol, negl_scale, max_sweeps);
   const bool flow = w.epoch != nullptr;
   const void* fn = flow ? (const void*)jacobi_kernel<NT, TPL, true> : (const void*)jacobi_kernel<NT, TPL, false>;
-  static int cfg_dev = -1, cfg_blocks = 0;
+  static std::atomic<int> cfg_dev{-1}, cfg_blocks{0};  // blocks stored before the device tag
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (cfg_dev != dev) {
@@ -1239,7 +1239,7 @@ int launch_jacobi(cudaStream_t s, SvdWork& w, int nrow, int ncol, double tol, do
     cfg_blocks = std::min(occ_a, occ_b) * num_sms();
     cfg_dev = dev;
   }
-  int blocks = (int)std::min<int64_t>(ceil_div(npairs, NT / 32), cfg_blocks);
+  int blocks = (int)std::min<int64_t>(ceil_div(npairs, NT / 32), cfg_blocks.load());
   if (blocks < 1) blocks = 1;
   if (flow) TT_CUDA_CHECK(cudaMemsetAsync(w.epoch, 0, (size_t)ncol * sizeof(unsigned), s));
   double* X = w.X;
@@ -1273,7 +1273,7 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
                  int64_t max_rank, double rel_floor) {
   const size_t smem = 2 * (size_t)ncol * sizeof(double);
   if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "svd_truncate: bond rank too large");
-  static int configured_dev = -1;
+  static std::atomic<int> configured_dev{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured_dev != dev) {
@@ -1290,7 +1290,7 @@ int svd_truncate(cudaStream_t s, SvdWork& w, int nrow, int ncol, double delta_sc
 
 int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ldr, double delta_scale,
                       double unit, double rel_floor) {
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   const size_t smem = 8 * (size_t)p * sizeof(double);
@@ -1301,7 +1301,7 @@ int certify_full_rank(cudaStream_t s, SvdWork& w, const double* R, int p, int ld
     configured = dev;
   }
   if (p <= 512) {
-    static int configured_cols = -1;
+    static std::atomic<int> configured_cols{-1};
     if (configured_cols != dev) {
       TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          200 * 1024));
@@ -1341,7 +1341,7 @@ int launch_jacobi_block(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol
                         int ldv, int max_sweeps) {
   constexpr int NT = 32 * GS;
   const size_t smem = jacobi_block_smem_gs(GS, nrow, ncol);
-  static int cfg_dev = -1, cfg_blocks = 0;
+  static std::atomic<int> cfg_dev{-1}, cfg_blocks{0};  // blocks stored before the device tag
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (cfg_dev != dev) {
@@ -1362,7 +1362,7 @@ int launch_jacobi_block(cudaStream_t s, SvdWork& w, float* X, int nrow, int ncol
   TT_CUDA_CHECK(cudaMemsetAsync(w.rot, 0, SvdWork::kMaxSweeps * sizeof(unsigned), s));
   const int G = (ncol + GS - 1) / GS;
   const int NG = G + (G & 1);
-  int blocks = std::min(NG / 2, cfg_blocks);
+  int blocks = std::min(NG / 2, cfg_blocks.load());
   if (blocks < 1) blocks = 1;
   // 8 sqrt(n) 2^-24: the rounding of an FP32 dot product of n terms is ~sqrt(n) 2^-24
   // of |a| |b|, so a smaller tolerance can keep rotating on noise (it did for n = 2); the
@@ -1415,7 +1415,7 @@ int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, dou
   if (nj <= 0 || n_max <= 0) return TT_OK;
   const size_t smem = 8 * (size_t)n_max * sizeof(double);
   if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "certify_batched: rank too large");
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {
@@ -1424,7 +1424,7 @@ int certify_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, dou
     configured = dev;
   }
   if (n_max <= 640) {
-    static int configured_cols = -1;
+    static std::atomic<int> configured_cols{-1};
     if (configured_cols != dev) {
       TT_CUDA_CHECK(cudaFuncSetAttribute(rinv_colnorm_cols_batched_kernel<4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -1485,7 +1485,7 @@ int allow_cluster16(K kernel) {
 template <int CS>
 int f64_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int skip, int max_sweeps) {
   if (CS > 8) {
-    static int configured = -1;
+    static std::atomic<int> configured{-1};
     int dev = 0;
     TT_CUDA_CHECK(cudaGetDevice(&dev));
     if (configured != dev) {
@@ -1509,7 +1509,7 @@ int f64_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int ski
 template <int CS>
 int f32_cluster(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max, int max_sweeps) {
   if (CS > 8) {
-    static int configured = -1;
+    static std::atomic<int> configured{-1};
     int dev = 0;
     TT_CUDA_CHECK(cudaGetDevice(&dev));
     if (configured != dev) {
@@ -1572,7 +1572,7 @@ int svd_truncate_batched(cudaStream_t s, int nj, const SvdJob* d_jobs, int n_max
   if (nj <= 0 || n_max <= 0) return TT_OK;
   const size_t smem = 2 * (size_t)n_max * sizeof(double);
   if (smem > 200 * 1024) return fail(TT_ERR_UNSUPPORTED, "svd_truncate_batched: bond rank too large");
-  static int configured = -1;
+  static std::atomic<int> configured{-1};
   int dev = 0;
   TT_CUDA_CHECK(cudaGetDevice(&dev));
   if (configured != dev) {
