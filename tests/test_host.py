@@ -135,3 +135,39 @@ def test_inputs_are_deterministic():
 def test_random_tt_norm_is_one_in_expectation():
     norms = [core.norm(inputs.random_tt(s, 8, 2, 4)) ** 2 for s in range(200)]
     assert 0.8 < np.mean(norms) < 1.25
+
+
+def test_workspace_queries_on_host_without_gpu():
+    """The workspace queries are host arithmetic: they answer without a GPU, grow with the
+    ranks, hold at least the largest core, and the evaluation adjoint's stops growing at one
+    chunk of at most 1 GiB of prefix and suffix states."""
+    lib = _abi.load()
+    L = 40
+    keep = []
+
+    def train(dtype, r):
+        d = (ctypes.c_int32 * L)(*([2] * L))
+        rk = (ctypes.c_int64 * (L + 1))(*([1] + [r] * (L - 1) + [1]))
+        p = (ctypes.c_void_p * L)(*([1] * L))
+        keep.append((d, rk, p))
+        return ctypes.byref(_abi.tt_train(L, dtype, d, rk, p))
+
+    prev = None
+    for r in (8, 64, 320):
+        x64, x32 = train(_abi.TT_F64, r), train(_abi.TT_F32, r)
+        sizes = (lib.tt_round_workspace_size(x64, _abi.TT_PREC_FP64),
+                 lib.tt_round_workspace_size(x32, _abi.TT_PREC_MIXED),
+                 lib.tt_round_backward_workspace_size(x64),
+                 lib.tt_inner_workspace_size(x64, x64))
+        assert sizes[0] >= 8 * r * 2 * r and sizes[1] >= 4 * r * 2 * r
+        if prev is not None:
+            assert all(a > b for a, b in zip(sizes, prev)), (r, sizes, prev)
+        prev = sizes
+    x = train(_abi.TT_F32, 64)
+    per_sample = (1 + 64 * (L - 1)) + (64 * (L - 1) + 1)  # sum_k r_k + r_{k+1}
+    cores = 2 * (2 * 64 + (L - 2) * 64 * 64)
+    ns = [1, 1000, 65536, 10 ** 6, 10 ** 8, 2 * 10 ** 8]
+    ws = [lib.tt_eval_backward_workspace_size(x, n) for n in ns]
+    assert all(b >= a for a, b in zip(ws, ws[1:]))
+    assert ws[1] >= 1000 * per_sample * 4
+    assert ws[-1] == ws[-2] <= (1 << 30) + 8 * cores + 4096
