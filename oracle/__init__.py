@@ -12,10 +12,12 @@ Modules
   structured  closed-form exp / cos / sin / polynomial TTs, shift MPOs and
               Dirichlet Laplacians                              (Section 4)
   grad        hand-derived adjoints of apply / hadamard / inner / evaluate / rounding
+  approx      the decomposition (zip-up) and variational approximations of W x
+                                                                 (Sections 3.2, 3.3)
   qft         the Fourier (DFT) matrix as a tensor train from element-wise products of
               rank-b_q factors, rounded at a maximum rank            (Section 4.3)
 
 Every function is pinned by ``tests/test_oracle_*.py`` against brute force on
 full tensors, closed forms, invariants or finite differences.
 """
-from . import core, grad, qft, structured  # noqa: F401
+from . import approx, core, grad, qft, structured  # noqa: F401

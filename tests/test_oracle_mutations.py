@@ -18,8 +18,9 @@ import textwrap
 
 import pytest
 
-from oracle import core, grad, qft, structured
+from oracle import approx, core, grad, qft, structured
 
+import test_oracle_approx as pa
 import test_oracle_exact as pe
 import test_oracle_grad as pg
 import test_oracle_qft as pq
@@ -130,6 +131,28 @@ CASES = [
     ("laplacian_mpo: pending terms of other dimensions dropped", structured, "laplacian_mpo",
      "if pending_other:", "if False:",
      [lambda: ps.test_laplacian_dense(2, 4, 5)]),
+    # ---- approximate einsums (Section 3.2 zip-up, Section 3.3 variational fit)
+    ("zip-up: threshold without 1/sqrt(L-1)", approx, "decomposition_apply",
+     "delta = eps * float(np.linalg.norm(sc)) / math.sqrt(L - 1)", "delta = eps * float(np.linalg.norm(sc))",
+     [lambda: pa.test_decomposition_over_the_whole_train_is_the_rounding(1e-1)]),
+    ("zip-up: S kept on the split-off core", approx, "decomposition_apply",
+     "out.append(u[:, :rn].reshape(left, d, rn))\n        sc = (s[:rn, None] * vt[:rn])",
+     "out.append((u[:, :rn] * s[None, :rn]).reshape(left, d, rn))\n        sc = (vt[:rn])",
+     [lambda: pa.test_decomposition_over_the_whole_train_is_the_rounding(1e-1)]),
+    ("variational: left environment with the digits of y reversed", approx, "_left_env",
+     'np.einsum("ab,aic,bid->cd", e, c[p], y[p], optimize=True)',
+     'np.einsum("ab,aic,bid->cd", e, c[p], y[p][:, ::-1, :], optimize=True)',
+     [lambda: pa.test_variational_centre_is_the_overlap_gradient(1),
+      lambda: pa.test_variational_updates_never_increase_the_distance(1, 4)]),
+    ("variational: updated core kept instead of its orthonormal Q", approx, "variational_apply",
+     "c[q] = qm.reshape(r0, d, qm.shape[1])", "c[q] = c[q].reshape(r0, d, r1)",
+     [lambda: pa.test_variational_centre_is_the_overlap_gradient(1),
+      lambda: pa.test_variational_updates_never_increase_the_distance(1, 4)]),
+    ("variational: S left on the left core when sweeping right", approx, "variational_apply",
+     "c[q] = u[:, :rn].reshape(r0, d0, rn)\n            c[q + 1] = (s[:rn, None] * vt[:rn]).reshape(rn, d1, r1)",
+     "c[q] = (u[:, :rn] * s[None, :rn]).reshape(r0, d0, rn)\n            c[q + 1] = vt[:rn].reshape(rn, d1, r1)",
+     [lambda: pa.test_variational_centre_is_the_overlap_gradient(2),
+      lambda: pa.test_variational_updates_never_increase_the_distance(2, 4)]),
     # ---- the Fourier tensor train (Section 4.3)
     ("fourier factors: column digits not reversed", qft, "_weights",
      "w = [int(np.prod(bases[:p], dtype=np.int64)) for p in range(n)]", "w = list(c)",
