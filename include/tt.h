@@ -75,7 +75,7 @@ typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
  *                   and the norm in FP64. */
 typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_prec;
 
-/* Limits of this build. */
+/* Size limits of the library. */
 #define TT_MAX_SITES 128 /* L <= TT_MAX_SITES */
 #define TT_MAX_MODE 16   /* d_k <= TT_MAX_MODE */
 
