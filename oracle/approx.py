@@ -12,6 +12,9 @@ decomposition_apply (Section 3.2, "decomposition algorithms", the zip-up of its 
     delta = eps ||C(i_1..i_N)|| / sqrt(L - 1) with the norm of the first super-core (the paper
     states that with the centres at the left end the norm of the result depends only on it;
     that holds exactly when the super-core spans the whole train, N = L).
+    Parity unpinned for N < L beyond exactness without truncation and the rank cap: the result
+    has no closed form there, and the move of the operands' centres to the left end is pinned
+    by no value (it changes nothing in the exact and N = L cases).
 
 variational_apply (Section 3.3, Eq. (variational))
     C is kept in mixed canonical form with its centre on a super-core of N = ncores adjacent
